@@ -1,0 +1,174 @@
+"""Python access to the FP64 CPU oracle (oracle/oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check and by
+the benchmark's CPU-baseline leg.  The CUDA library never imports it and shares
+no code with it.  See oracle.c for what is computed and which passage of the
+paper each step follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+HOLE, FIELD, FRINGE = 0, 1, -1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (gcc, OpenMP, no FMA
+    contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            d, i32, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            P = ctypes.c_void_p
+            L.orc_tritri.restype = d
+            L.orc_tritri.argtypes = [P, P, P, P]
+            L.orc_pt_tri.restype = d
+            L.orc_pt_tri.argtypes = [P, P, P]
+            L.orc_seg_seg.restype = d
+            L.orc_seg_seg.argtypes = [P, P, P, P, P, P]
+            L.orc_elem_tris.restype = None
+            L.orc_elem_tris.argtypes = [i32, P, P]
+            L.orc_face_tris.restype = None
+            L.orc_face_tris.argtypes = [i32, P, P]
+            L.orc_winding.restype = d
+            L.orc_winding.argtypes = [P, i64, P]
+            L.orc_signed_volume.restype = d
+            L.orc_signed_volume.argtypes = [i64, P]
+            L.orc_apply_pose.restype = None
+            L.orc_apply_pose.argtypes = [i64, P, P, P]
+            L.orc_box_dist.restype = d
+            L.orc_box_dist.argtypes = [P, P]
+            L.orc_point_surface.restype = d
+            L.orc_point_surface.argtypes = [P, i64, P, P]
+            L.orc_cut.restype = i32
+            L.orc_cut.argtypes = [i32, i64, P, i32, i64, P, P, d, i32, P, i64, P, P, P, P, i32]
+            _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def tritri(A, B):
+    """Distance between closed triangles A, B (3x3 each) and the closest points."""
+    A, B = _f64(A), _f64(B)
+    ca, cb = np.zeros(3), np.zeros(3)
+    d = lib().orc_tritri(_ptr(A), _ptr(B), _ptr(ca), _ptr(cb))
+    return d, ca, cb
+
+
+def pt_tri(P, T):
+    P, T = _f64(P), _f64(T)
+    c = np.zeros(3)
+    return lib().orc_pt_tri(_ptr(P), _ptr(T), _ptr(c)), c
+
+
+def seg_seg(p0, p1, q0, q1):
+    a = [_f64(x) for x in (p0, p1, q0, q1)]
+    cp, cq = np.zeros(3), np.zeros(3)
+    d = lib().orc_seg_seg(*[_ptr(x) for x in a], _ptr(cp), _ptr(cq))
+    return d, cp, cq
+
+
+def elem_tris(p, nodes):
+    nodes = _f64(nodes)
+    out = np.zeros((12 * p * p, 3, 3))
+    lib().orc_elem_tris(p, _ptr(nodes), _ptr(out))
+    return out
+
+
+def face_tris(q, fnodes):
+    fnodes = _f64(fnodes)
+    out = np.zeros((2 * q * q, 3, 3))
+    lib().orc_face_tris(q, _ptr(fnodes), _ptr(out))
+    return out
+
+
+def surface_tris(q, faces):
+    faces = _f64(faces)
+    return np.concatenate([face_tris(q, f) for f in faces], axis=0)
+
+
+def winding(P, tris):
+    P, tris = _f64(P), _f64(tris)
+    return lib().orc_winding(_ptr(P), tris.shape[0], _ptr(tris))
+
+
+def signed_volume(tris):
+    tris = _f64(tris)
+    return lib().orc_signed_volume(tris.shape[0], _ptr(tris))
+
+
+def apply_pose(faces, pose):
+    faces = _f64(faces)
+    if pose is None:
+        return faces.copy()
+    pose = _f64(np.asarray(pose).reshape(3, 4))
+    out = np.empty_like(faces)
+    lib().orc_apply_pose(faces.size // 3, _ptr(faces), _ptr(pose), _ptr(out))
+    return out
+
+
+def box_dist(b1, b2):
+    b1, b2 = _f64(b1), _f64(b2)
+    return lib().orc_box_dist(_ptr(b1), _ptr(b2))
+
+
+def point_surface(P, tris):
+    P, tris = _f64(P), _f64(tris)
+    w = ctypes.c_double(0.0)
+    d = lib().orc_point_surface(_ptr(P), tris.shape[0], _ptr(tris), ctypes.byref(w))
+    return d, w.value
+
+
+STAT_NAMES = ("tritri_tests", "s_star_pairs", "s_star_tri_pairs", "undecidable", "paper_rule_disagree",
+              "fringe", "hole", "field")
+
+
+def cut(p, nodes, q, faces, pose=None, tol=1e-7, brute=False, ids=None, nthreads=0):
+    """Classify elements: returns (flags int8, dist f64, paper_flags int8, stats dict).
+    ``ids`` selects a subset of elements (outputs follow its order)."""
+    nodes, faces = _f64(nodes), _f64(faces)
+    n_elem = nodes.shape[0]
+    ids_arr = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+    nev = n_elem if ids_arr is None else ids_arr.shape[0]
+    flags = np.zeros(nev, dtype=np.int8)
+    pflags = np.zeros(nev, dtype=np.int8)
+    dist = np.zeros(nev, dtype=np.float64)
+    stats = np.zeros(8, dtype=np.int64)
+    pose_arr = None if pose is None else _f64(np.asarray(pose).reshape(3, 4))
+    rc = lib().orc_cut(p, n_elem, _ptr(nodes), q, faces.shape[0], _ptr(faces), _ptr(pose_arr), float(tol),
+                       1 if brute else 0, _ptr(ids_arr), nev, _ptr(flags), _ptr(dist), _ptr(pflags), _ptr(stats),
+                       int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_cut rejected its arguments")
+    return flags, dist, pflags, dict(zip(STAT_NAMES, (int(x) for x in stats)))

@@ -1,0 +1,168 @@
+/*
+ * directcut.h -- C ABI of libdirectcut.so, a GB300 (sm_103a) implementation of
+ * the parallel direct cut of Crabill, Witherden & Jameson (arXiv 1711.07663).
+ *
+ * The operation (Sec. 4.2 "Parallel Direct Cut Algorithm" of the paper): every
+ * element of a curved order-p hexahedral background grid computes its minimum
+ * distance to a closed cut surface of order-q quadrilateral faces and is
+ * classified as HOLE (inside the surface), FIELD (outside) or FRINGE (the
+ * paper's "intersecting" status: distance <= tol).  Element faces and cut faces
+ * are linearised into triangles (2 per sub-quad of the (p+1)^2 / (q+1)^2 node
+ * grids, Fig. "quadsplit"), the element-surface distance is the minimum
+ * triangle-triangle distance (Sec. 4.2, Alg. cp1/cp2 with tol = 1e-7), and the
+ * side comes from the dot product of the minimal vector with the outward face
+ * normal (Sec. 4.1/4.2), averaged over the faces that share the closest point.
+ *
+ * Conventions
+ *   element nodes  float64 [n_elem][(p+1)^3][3]; node (i,j,k) at
+ *                  i + (p+1)*(j + (p+1)*k), i along xi fastest (the tensor
+ *                  product Lagrange nodes of Eq. (reftophys)).
+ *   face nodes     float64 [n_faces][(q+1)^2][3]; node (i,j) at i + (q+1)*j.
+ *                  dx/dxi x dx/deta must point OUT of the region to blank, and
+ *                  the faces must form a closed, watertight surface (shared
+ *                  nodes bit-identical).
+ *   pose           12 float64, row-major [R | t]: x' = R x + t applied to every
+ *                  face node before the cut (rigid motion of the body, Sec. 4.3).
+ *   flags          int8 per element: DC_HOLE 0, DC_FIELD 1, DC_FRINGE -1.
+ *   dist           float64 per element: +d (FIELD), -d (HOLE), d (FRINGE) for
+ *                  elements that reach the exact test; elements decided by the
+ *                  Cartesian hole map (Sec. 4.2, "hole maps") get -HUGE_VAL
+ *                  (hole) or +HUGE_VAL (field).
+ *
+ * Ownership: the caller owns every pointer it passes.  dc_create copies the
+ * meshes to the device; dc_cut and dc_submit read the request's inputs before
+ * returning.  Output buffers must stay valid until dc_cut returns, or until
+ * dc_poll reports completion of a submitted ticket.
+ *
+ * Errors: no exception crosses this ABI.  Every call returns a dc_status; the
+ * text of the calling thread's last error is available from dc_last_error().
+ *
+ * Threads: calls on one context are serialised by the context; several
+ * contexts may be used from several threads.
+ */
+#ifndef DIRECTCUT_H
+#define DIRECTCUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dc_ctx dc_ctx;
+typedef int32_t dc_status;
+
+enum {
+    DC_OK = 0,
+    DC_PENDING = 1,      /* dc_poll: not finished yet */
+    DC_EINVAL = -1,      /* invalid argument (orders, counts, NaN nodes, pointers) */
+    DC_ENOMEM = -2,      /* device or host allocation failed */
+    DC_ECUDA = -3,       /* a CUDA runtime call failed */
+    DC_EBUSY = -4,       /* no serving slot / memory budget free: retry later */
+    DC_ETIMEDOUT = -5,   /* dc_poll: timeout elapsed, or a device wait ran out */
+    DC_ENOTFOUND = -6,   /* unknown mesh index or ticket */
+    DC_ECANCELED = -7,   /* the context was destroyed with the ticket in flight */
+    DC_EINTERNAL = -8    /* a device-side capacity was exceeded (message says which) */
+};
+
+enum { DC_HOLE = 0, DC_FIELD = 1, DC_FRINGE = -1 };
+
+/* Precision of the bulk triangle-triangle tests (Sec. 4.2 remarks that the
+ * prepass may use single precision).  DC_FP32_RECHECK evaluates all candidate
+ * pairs in FP32 with certified error bounds and re-solves, in FP64, only the
+ * pairs whose FP32 lower bound lies within the bound of the best distance;
+ * DC_FP64 evaluates every pair in FP64.  Both give the same flags. */
+enum { DC_FP64 = 0, DC_FP32_RECHECK = 1 };
+
+typedef struct {
+    int32_t p;                /* element order, 1..4 */
+    int64_t n_elem;           /* >= 1 */
+    const double *nodes;      /* [n_elem][(p+1)^3][3] */
+    int32_t nodes_on_device;  /* 0: host pointer, 1: device pointer (both copied) */
+} dc_mesh_desc;
+
+typedef struct {
+    int32_t device;           /* CUDA device ordinal */
+    int32_t precision;        /* DC_FP32_RECHECK (default) or DC_FP64 */
+    size_t mem_budget_bytes;  /* device bytes the context may hold; 0 = no limit */
+    double tol;               /* fringe tolerance, absolute mesh units; 0 -> 1e-7 (Alg. cp1) */
+    int32_t holemap_cells;    /* hole-map cubes along the longest surface side, 8..80;
+                                 0 -> 64 (the paper uses 60-80) */
+    int32_t bin_cubes;        /* hole-map cubes per face bin along each axis, 1..16; 0 -> 4 */
+    int32_t max_inflight;     /* serving slots for dc_submit, 1..64; 0 -> 4 */
+    int32_t profile;          /* 1: time each phase with CUDA events (dc_get_stats) */
+} dc_config;
+
+typedef struct {
+    int32_t q;                /* face order, 1..4 */
+    int64_t n_faces;          /* >= 1 */
+    const double *face_nodes; /* [n_faces][(q+1)^2][3] */
+    const double *pose;       /* host pointer to 12 doubles [R|t], or NULL (identity) */
+    int8_t *flags_out;        /* [n_elem] */
+    double *dist_out;         /* [n_elem] or NULL */
+    int32_t on_device;        /* 1: face_nodes, flags_out, dist_out are device pointers */
+    int32_t async;            /* dc_cut only, device pointers only: 1 = return after
+                                 enqueueing on `stream`; results are valid once the
+                                 stream reaches that point */
+    void *stream;             /* cudaStream_t for dc_cut; NULL = the context's stream */
+} dc_request;
+
+typedef struct {
+    int64_t n_elem;           /* elements classified by the last dc_cut / dc_cut_batch */
+    int64_t n_candidates;     /* elements the hole map could not decide (exact test) */
+    int64_t n_fringe, n_hole, n_field;
+    int64_t faces_visited;    /* element-face pairs whose triangles were tested */
+    int64_t pairs_bulk;       /* triangle pairs evaluated in the bulk precision */
+    int64_t pairs_recheck;    /* triangle pairs re-solved in FP64 */
+    int64_t fallbacks;        /* elements redone in FP64 after a list overflow */
+    int64_t holemap_components; /* enclosed components found by the hole map */
+    float ms_surface;         /* profile=1 only: pose + face boxes + hole map tags + bins */
+    float ms_holemap;         /* connected components + winding-number seeds */
+    float ms_classify;        /* hole-map lookup + candidate compaction */
+    float ms_exact;           /* exact element-face tests + sign */
+    float ms_total;
+} dc_stats;
+
+/* Fill *cfg with the defaults listed above. */
+dc_status dc_config_default(dc_config *cfg);
+
+/* Create a context on cfg->device holding n_meshes resident background grids
+ * (copied; their element boxes are cached).  *out receives the context. */
+dc_status dc_create(const dc_config *cfg, const dc_mesh_desc *meshes, int32_t n_meshes, dc_ctx **out);
+
+/* Cut resident mesh `mesh` with one surface; synchronous unless req->async. */
+dc_status dc_cut(dc_ctx *ctx, int32_t mesh, const dc_request *req);
+
+/* Cut n (mesh, surface) instances in one batched launch sequence: every phase
+ * runs once over all instances (persistent exact-test kernel over the union of
+ * their candidates).  Synchronous; requests must not set async. */
+dc_status dc_cut_batch(dc_ctx *ctx, int32_t n, const int32_t *meshes, const dc_request *reqs);
+
+/* Serving: admit a request into a free slot (DC_EBUSY when none is free or the
+ * memory budget is exhausted), copy its inputs, enqueue the cut on the slot's
+ * stream and return a ticket.  Requests in different slots overlap on the GPU. */
+dc_status dc_submit(dc_ctx *ctx, int32_t mesh, const dc_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_us (0 = just test, <0 = wait until done) for a ticket:
+ * DC_OK when its outputs are written (the slot is released), DC_PENDING if
+ * not done, or the error the cut ended with. */
+dc_status dc_poll(dc_ctx *ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Counters and (profile=1) phase times of the last dc_cut / dc_cut_batch. */
+dc_status dc_get_stats(dc_ctx *ctx, dc_stats *out);
+
+/* Drain in-flight work, then free everything the context owns. */
+void dc_destroy(dc_ctx *ctx);
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char *dc_last_error(void);
+
+/* Library version string. */
+const char *dc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIRECTCUT_H */

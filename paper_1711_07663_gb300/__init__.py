@@ -1,0 +1,277 @@
+"""Python binding of libdirectcut, the GB300 (sm_103a) parallel direct cut.
+
+Argument marshalling only: every step of the cut runs in the CUDA library
+(include/directcut.h documents the operation, layouts and errors).  The
+functions keep the C names (dc_create, dc_cut, dc_cut_batch, dc_submit,
+dc_poll, dc_get_stats, dc_destroy); ``Context`` wraps them for convenience.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA); the
+binding passes their addresses and whether they live on the device.  There is
+no CPU fallback: importing works without a GPU, but any call that needs the
+library raises if libdirectcut.so is missing or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "DC_HOLE", "DC_FIELD", "DC_FRINGE", "DC_FP64", "DC_FP32_RECHECK", "DirectCutError", "load", "lib_path",
+    "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
+    "dc_last_error", "dc_version", "Context", "EXPORTED",
+]
+
+DC_OK, DC_PENDING = 0, 1
+DC_EINVAL, DC_ENOMEM, DC_ECUDA, DC_EBUSY, DC_ETIMEDOUT, DC_ENOTFOUND, DC_ECANCELED, DC_EINTERNAL = range(-1, -9, -1)
+DC_HOLE, DC_FIELD, DC_FRINGE = 0, 1, -1
+DC_FP64, DC_FP32_RECHECK = 0, 1
+
+EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
+            "dc_destroy", "dc_last_error", "dc_version")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", "libdirectcut.so")
+
+
+class DirectCutError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"directcut status {status}: {message}")
+        self.status = status
+
+
+class dc_mesh_desc(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("n_elem", ctypes.c_int64), ("nodes", ctypes.c_void_p),
+                ("nodes_on_device", ctypes.c_int32)]
+
+
+class dc_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t),
+                ("tol", ctypes.c_double), ("holemap_cells", ctypes.c_int32), ("bin_cubes", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class dc_request(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("n_faces", ctypes.c_int64), ("face_nodes", ctypes.c_void_p),
+                ("pose", ctypes.c_void_p), ("flags_out", ctypes.c_void_p), ("dist_out", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("async_", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class dc_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_elem", "n_candidates", "n_fringe", "n_hole", "n_field",
+                                             "faces_visited", "pairs_bulk", "pairs_recheck", "fallbacks",
+                                             "holemap_components")] + \
+               [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_total")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = False):
+    """Load libdirectcut.so (built in-tree by paper_1711_07663_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise DirectCutError(DC_EINVAL, f"{path} is missing: run paper_1711_07663_gb300.build.build() "
+                                                "(the CUDA library is required; there is no CPU fallback)")
+            from . import build as _b
+            _b.build()
+        L = ctypes.CDLL(path)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.dc_config_default.argtypes = [ctypes.POINTER(dc_config)]
+        L.dc_config_default.restype = i32
+        L.dc_create.argtypes = [ctypes.POINTER(dc_config), ctypes.POINTER(dc_mesh_desc), i32, ctypes.POINTER(P)]
+        L.dc_create.restype = i32
+        L.dc_cut.argtypes = [P, i32, ctypes.POINTER(dc_request)]
+        L.dc_cut.restype = i32
+        L.dc_cut_batch.argtypes = [P, i32, ctypes.POINTER(i32), ctypes.POINTER(dc_request)]
+        L.dc_cut_batch.restype = i32
+        L.dc_submit.argtypes = [P, i32, ctypes.POINTER(dc_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.dc_submit.restype = i32
+        L.dc_poll.argtypes = [P, ctypes.c_uint64, i64]
+        L.dc_poll.restype = i32
+        L.dc_get_stats.argtypes = [P, ctypes.POINTER(dc_stats)]
+        L.dc_get_stats.restype = i32
+        L.dc_destroy.argtypes = [P]
+        L.dc_destroy.restype = None
+        L.dc_last_error.argtypes = []
+        L.dc_last_error.restype = ctypes.c_char_p
+        L.dc_version.argtypes = []
+        L.dc_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def dc_last_error() -> str:
+    return load().dc_last_error().decode()
+
+
+def dc_version() -> str:
+    return load().dc_version().decode()
+
+
+def _check(st: int) -> int:
+    if st < 0:
+        raise DirectCutError(st, dc_last_error())
+    return st
+
+
+def _addr(x, dtype):
+    """(address, on_device, keepalive) of a contiguous numpy array or torch tensor."""
+    if x is None:
+        return None, False, None
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        import torch
+        want = {np.float64: torch.float64, np.int8: torch.int8}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return x.data_ptr(), bool(x.is_cuda), x
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be C-contiguous {np.dtype(dtype)}")
+    return a.ctypes.data, False, a
+
+
+def make_config(**kw) -> dc_config:
+    cfg = dc_config()
+    _check(load().dc_config_default(ctypes.byref(cfg)))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def dc_create(meshes, **cfg_kw):
+    """meshes: list of (p, nodes) with nodes [n_elem][(p+1)^3][3] float64.
+    Returns an opaque context handle (int)."""
+    descs = (dc_mesh_desc * len(meshes))()
+    keep = []
+    for i, (p, nodes) in enumerate(meshes):
+        ptr, dev, k = _addr(nodes, np.float64)
+        keep.append(k)
+        n_elem = (k.shape[0] if hasattr(k, "shape") else len(k))
+        descs[i].p, descs[i].n_elem, descs[i].nodes, descs[i].nodes_on_device = int(p), int(n_elem), ptr, int(dev)
+    cfg = make_config(**cfg_kw)
+    h = ctypes.c_void_p()
+    _check(load().dc_create(ctypes.byref(cfg), descs, len(meshes), ctypes.byref(h)))
+    return h.value
+
+
+def _request(q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=False):
+    r = dc_request()
+    fp, fdev, fk = _addr(faces, np.float64)
+    op, odev, ok = _addr(flags_out, np.int8)
+    dp, ddev, dk = _addr(dist_out, np.float64)
+    if dist_out is not None and ddev != odev:
+        raise ValueError("flags_out and dist_out must live in the same memory")
+    if fdev != odev:
+        raise ValueError("face nodes and outputs must both be host or both be device memory")
+    pk = None
+    if pose is not None:
+        pk = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
+    r.q = int(q)
+    r.n_faces = int(fk.shape[0])
+    r.face_nodes = fp
+    r.pose = None if pk is None else pk.ctypes.data
+    r.flags_out = op
+    r.dist_out = dp
+    r.on_device = int(fdev)
+    r.async_ = int(bool(async_))
+    r.stream = None if stream is None else int(stream)
+    return r, (fk, ok, dk, pk)
+
+
+def dc_cut(ctx, mesh, q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=False):
+    r, keep = _request(q, faces, flags_out, dist_out, pose, stream, async_)
+    _check(load().dc_cut(ctx, int(mesh), ctypes.byref(r)))
+
+
+def dc_cut_batch(ctx, meshes, requests):
+    """requests: list of dicts with keys q, faces, flags_out[, dist_out, pose]."""
+    n = len(requests)
+    arr = (dc_request * n)()
+    keep = []
+    for i, rq in enumerate(requests):
+        r, k = _request(rq["q"], rq["faces"], rq["flags_out"], rq.get("dist_out"), rq.get("pose"))
+        arr[i] = r
+        keep.append(k)
+    ms = (ctypes.c_int32 * n)(*[int(m) for m in meshes])
+    _check(load().dc_cut_batch(ctx, n, ms, arr))
+
+
+def dc_submit(ctx, mesh, q, faces, flags_out, dist_out=None, pose=None):
+    r, keep = _request(q, faces, flags_out, dist_out, pose)
+    t = ctypes.c_uint64()
+    _check(load().dc_submit(ctx, int(mesh), ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def dc_poll(ctx, ticket, timeout_us=0):
+    """DC_OK (0) when done, DC_PENDING (1) when not; raises on errors."""
+    return _check(load().dc_poll(ctx, int(ticket), int(timeout_us)))
+
+
+def dc_get_stats(ctx) -> dict:
+    s = dc_stats()
+    _check(load().dc_get_stats(ctx, ctypes.byref(s)))
+    return {n: getattr(s, n) for n, _ in dc_stats._fields_}
+
+
+def dc_destroy(ctx) -> None:
+    if ctx:
+        load().dc_destroy(ctx)
+
+
+class Context:
+    """Owning wrapper: Context([(p, nodes), ...], precision=..., ...)."""
+
+    def __init__(self, meshes, **cfg):
+        self.meshes = [(int(p), nodes) for p, nodes in meshes]
+        self.n_elem = [int(n.shape[0]) for _, n in self.meshes]
+        self.handle = dc_create(self.meshes, **cfg)
+
+    def cut(self, mesh, q, faces, flags_out=None, dist_out=None, pose=None, stream=None, async_=False):
+        if flags_out is None:
+            n = self.n_elem[mesh] if 0 <= mesh < len(self.n_elem) else 1
+            flags_out = np.empty(n, dtype=np.int8)
+        dc_cut(self.handle, mesh, q, faces, flags_out, dist_out, pose, stream, async_)
+        return flags_out
+
+    def cut_batch(self, meshes, requests):
+        dc_cut_batch(self.handle, meshes, requests)
+
+    def submit(self, mesh, q, faces, flags_out, dist_out=None, pose=None):
+        return dc_submit(self.handle, mesh, q, faces, flags_out, dist_out, pose)
+
+    def poll(self, ticket, timeout_us=0):
+        return dc_poll(self.handle, ticket, timeout_us)
+
+    def stats(self):
+        return dc_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            dc_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,772 @@
+// dc_api.cu -- the C ABI of libdirectcut (declared in include/directcut.h).
+//
+// Host side of the parallel direct cut: resident background grids, per-slot
+// device arenas, the launch sequence of one (batched) cut, and the serving
+// calls (dc_submit / dc_poll) that let requests in different slots overlap on
+// the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/directcut.h"
+#include "dc_exact.cuh"
+
+using namespace dc;
+
+namespace {
+
+thread_local std::string g_err;
+
+dc_status fail(dc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(DC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------ element boxes
+__global__ void k_elem_box(const double* __restrict__ nodes, long long n_elem, int npe, float* __restrict__ box,
+                           int* __restrict__ bad) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  const double* x = nodes + e * npe * 3;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool nonfinite = false;
+  for (int k = 0; k < npe; ++k)
+    for (int a = 0; a < 3; ++a) {
+      double v = x[3 * k + a];
+      nonfinite |= !(fabs(v) < 1e300);
+      lo[a] = fmin(lo[a], v);
+      hi[a] = fmax(hi[a], v);
+    }
+  for (int a = 0; a < 3; ++a) {
+    box[6 * e + a] = __double2float_rd(lo[a]);
+    box[6 * e + 3 + a] = __double2float_ru(hi[a]);
+  }
+  if (nonfinite) atomicOr(bad, 1);
+}
+
+// ------------------------------------------------------------------ triangle tables
+// Element faces: 0 xi=-1, 1 xi=+1, 2 eta=-1, 3 eta=+1, 4 zeta=-1, 5 zeta=+1;
+// face grid coordinates (a, b) run over the two free reference directions in
+// (xi, eta, zeta) order; each grid quad (a,b) becomes triangles (00,10,11) and
+// (00,11,01).  Cut faces: node (i,j) at i + (q+1) j, same quad split, which
+// keeps d/dxi x d/deta as the triangle normal.
+void build_tables(unsigned char et[MAX_P][MAX_NTE][3], unsigned char ft[MAX_Q][MAX_NTF][3]) {
+  memset(et, 0, sizeof(unsigned char) * MAX_P * MAX_NTE * 3);
+  memset(ft, 0, sizeof(unsigned char) * MAX_Q * MAX_NTF * 3);
+  for (int p = 1; p <= MAX_P; ++p) {
+    auto nid = [p](int i, int j, int k) { return i + (p + 1) * (j + (p + 1) * k); };
+    int t = 0;
+    for (int face = 0; face < 6; ++face) {
+      int axis = face / 2, fix = (face % 2) ? p : 0;
+      auto at = [&](int a, int b) {
+        int ijk[3];
+        ijk[axis] = fix;
+        int u = 0;
+        for (int d = 0; d < 3; ++d)
+          if (d != axis) ijk[d] = (u++ == 0) ? a : b;
+        return nid(ijk[0], ijk[1], ijk[2]);
+      };
+      for (int b = 0; b < p; ++b)
+        for (int a = 0; a < p; ++a) {
+          int q00 = at(a, b), q10 = at(a + 1, b), q11 = at(a + 1, b + 1), q01 = at(a, b + 1);
+          int tri[2][3] = {{q00, q10, q11}, {q00, q11, q01}};
+          for (int h = 0; h < 2; ++h, ++t)
+            for (int c = 0; c < 3; ++c) et[p - 1][t][c] = (unsigned char)tri[h][c];
+        }
+    }
+  }
+  for (int q = 1; q <= MAX_Q; ++q) {
+    int t = 0;
+    for (int b = 0; b < q; ++b)
+      for (int a = 0; a < q; ++a) {
+        int q00 = a + (q + 1) * b, q10 = q00 + 1, q01 = q00 + (q + 1), q11 = q01 + 1;
+        int tri[2][3] = {{q00, q10, q11}, {q00, q11, q01}};
+        for (int h = 0; h < 2; ++h, ++t)
+          for (int c = 0; c < 3; ++c) ft[q - 1][t][c] = (unsigned char)tri[h][c];
+      }
+  }
+}
+
+// ------------------------------------------------------------------ context
+struct Mesh {
+  int p = 0;
+  long long n_elem = 0;
+  double* nodes = nullptr;
+  float* box = nullptr;
+};
+
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  Arena arena;
+  // Pinned staging of the instance table, reused round-robin: an entry is
+  // rewritten only after the event recorded behind its upload has completed,
+  // so back-to-back asynchronous cuts never overwrite a pending copy.
+  static constexpr int RING = 4;
+  Inst* ring_inst[RING] = {nullptr, nullptr, nullptr, nullptr};
+  long long* ring_off[RING] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ring_ev[RING] = {nullptr, nullptr, nullptr, nullptr};
+  bool ring_used[RING] = {false, false, false, false};
+  int ring_pos = 0;
+  Inst* h_inst = nullptr;        // current ring entry
+  long long* h_off = nullptr;    // current ring entry: foff then eoff
+  size_t h_inst_cap = 0;
+  unsigned long long* h_cnt = nullptr;  // pinned counters readback
+  int8_t* h_flags = nullptr;     // pinned output staging (serving, host outputs)
+  double* h_dist = nullptr;
+  size_t h_out_cap = 0;
+  bool busy = false;
+  uint64_t ticket = 0;
+  // in-flight bookkeeping
+  int n_inst = 0;
+  Inst* d_inst = nullptr;
+  unsigned long long* d_cnt = nullptr;
+  int8_t* user_flags = nullptr;
+  double* user_dist = nullptr;
+  long long out_n = 0;
+  bool host_out = false;
+  bool want_dist = false;
+  int cur_ring = 0;
+};
+
+constexpr int NCNT = 16;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters
+
+}  // namespace
+
+struct dc_ctx {
+  dc_config cfg;
+  int n_sm = 0;
+  std::vector<Mesh> meshes;
+  std::vector<Slot> slots;
+  std::mutex mu;
+  uint64_t next_ticket = 1;
+  size_t mesh_bytes = 0;
+  size_t arena_bytes = 0;
+  dc_stats last{};
+  int pmax = 1;
+  int cc_smem = 0;     // dynamic shared memory of the hole-map component kernel
+  int smem_optin = 0;  // per-block opt-in shared memory limit of the device
+};
+
+namespace {
+
+struct InstReq {
+  int mesh;
+  const dc_request* req;
+};
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int nbins_cap(int bin_cubes) {
+  int b = (MAX_DIM + bin_cubes - 1) / bin_cubes;
+  return b * b * b;
+}
+
+size_t cube_bytes() { return (size_t)MAX_DIM * MAX_DIM * CUBE_PITCH; }
+
+// bytes of arena a batch needs
+size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
+  size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
+  int nb = nbins_cap(c->cfg.bin_cubes);
+  for (auto& r : v) {
+    long long F = r.req->n_faces;
+    int npf = (r.req->q + 1) * (r.req->q + 1);
+    if (!r.req->on_device) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
+    s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(double) * F * 6) + al256(sizeof(float) * F * 6) +
+         al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1));
+  }
+  s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
+  s += al256(sizeof(unsigned long long) * NCNT);
+  s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
+  return s;
+}
+
+dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
+  if (s.arena.cap >= need) return DC_OK;
+  size_t grow = std::max(need, s.arena.cap + s.arena.cap / 2);
+  if (c->cfg.mem_budget_bytes &&
+      c->mesh_bytes + c->arena_bytes - s.arena.cap + grow > c->cfg.mem_budget_bytes) {
+    grow = need;
+    if (c->mesh_bytes + c->arena_bytes - s.arena.cap + grow > c->cfg.mem_budget_bytes)
+      return fail(DC_EBUSY, "memory budget of %zu bytes exhausted (need %zu more)", c->cfg.mem_budget_bytes, grow);
+  }
+  if (s.arena.base) {
+    CK(cudaStreamSynchronize(s.stream));
+    CK(cudaFree(s.arena.base));
+    c->arena_bytes -= s.arena.cap;
+    s.arena.base = nullptr;
+    s.arena.cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&s.arena.base, grow);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DC_ENOMEM, "cudaMalloc(%zu) for the cut arena failed: %s", grow, cudaGetErrorString(e));
+  }
+  s.arena.cap = grow;
+  c->arena_bytes += grow;
+  return DC_OK;
+}
+
+dc_status ensure_host(Slot& s, size_t n_inst, long long ne_total) {
+  if (s.h_inst_cap < n_inst) {
+    for (int r = 0; r < Slot::RING; ++r) {
+      if (s.ring_used[r]) CK(cudaEventSynchronize(s.ring_ev[r]));
+      if (s.ring_inst[r]) cudaFreeHost(s.ring_inst[r]);
+      if (s.ring_off[r]) cudaFreeHost(s.ring_off[r]);
+      s.ring_inst[r] = nullptr;
+      s.ring_off[r] = nullptr;
+      s.ring_used[r] = false;
+    }
+    for (int r = 0; r < Slot::RING; ++r) {
+      CK(cudaMallocHost(&s.ring_inst[r], sizeof(Inst) * n_inst));
+      CK(cudaMallocHost(&s.ring_off[r], sizeof(long long) * 2 * (n_inst + 1)));
+    }
+    s.h_inst_cap = n_inst;
+  }
+  {
+    int r = s.ring_pos;
+    s.ring_pos = (s.ring_pos + 1) % Slot::RING;
+    if (s.ring_used[r]) CK(cudaEventSynchronize(s.ring_ev[r]));
+    s.h_inst = s.ring_inst[r];
+    s.h_off = s.ring_off[r];
+    s.ring_used[r] = false;
+    s.cur_ring = r;
+  }
+  if (!s.h_cnt) CK(cudaMallocHost(&s.h_cnt, sizeof(unsigned long long) * NCNT));
+  if ((long long)s.h_out_cap < ne_total) {
+    if (s.h_flags) cudaFreeHost(s.h_flags);
+    if (s.h_dist) cudaFreeHost(s.h_dist);
+    s.h_flags = nullptr;
+    s.h_dist = nullptr;
+    CK(cudaMallocHost(&s.h_flags, (size_t)ne_total));
+    CK(cudaMallocHost(&s.h_dist, sizeof(double) * ne_total));
+    s.h_out_cap = (size_t)ne_total;
+  }
+  return DC_OK;
+}
+
+dc_status validate_req(dc_ctx* c, int mesh, const dc_request* r) {
+  if (!r) return fail(DC_EINVAL, "request is NULL");
+  if (mesh < 0 || mesh >= (int)c->meshes.size()) return fail(DC_ENOTFOUND, "mesh %d does not exist", mesh);
+  if (r->q < 1 || r->q > MAX_Q) return fail(DC_EINVAL, "face order q=%d outside 1..%d", r->q, MAX_Q);
+  if (r->n_faces < 1 || r->n_faces > (1LL << 30)) return fail(DC_EINVAL, "n_faces=%lld out of range", (long long)r->n_faces);
+  if (!r->face_nodes || !r->flags_out) return fail(DC_EINVAL, "face_nodes and flags_out are required");
+  if (r->pose)
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(r->pose[i])) return fail(DC_EINVAL, "pose has a non-finite entry");
+  if (!r->on_device) {
+    int npf = (r->q + 1) * (r->q + 1);
+    const double* x = r->face_nodes;
+    long long n = r->n_faces * npf * 3;
+    for (long long i = 0; i < n; ++i)
+      if (!std::isfinite(x[i])) return fail(DC_EINVAL, "face node value %lld is not finite", i);
+  }
+  return DC_OK;
+}
+
+// Enqueue the whole cut of a batch on slot s (no host synchronisation).
+dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool staged_out) {
+  const int n = (int)v.size();
+  long long nf_total = 0, ne_total = 0, max_tri = 0;
+  int pmax = 1, qmax = 1;
+  for (auto& r : v) {
+    nf_total += r.req->n_faces;
+    ne_total += c->meshes[r.mesh].n_elem;
+    max_tri = std::max<long long>(max_tri, r.req->n_faces * 2LL * r.req->q * r.req->q);
+    pmax = std::max(pmax, c->meshes[r.mesh].p);
+    qmax = std::max(qmax, r.req->q);
+  }
+  dc_status rc = ensure_arena(c, s, arena_need(c, v, ne_total));
+  if (rc) return rc;
+  rc = ensure_host(s, (size_t)n, ne_total);
+  if (rc) return rc;
+  // carve the arena
+  char* p = s.arena.base;
+  auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return r; };
+  Inst* d_inst = (Inst*)take(sizeof(Inst) * n);
+  long long* d_off = (long long*)take(sizeof(long long) * 2 * (n + 1));
+  const int nb = nbins_cap(c->cfg.bin_cubes);
+  long long fo = 0, eo = 0;
+  for (int i = 0; i < n; ++i) {
+    const dc_request* r = v[i].req;
+    const Mesh& m = c->meshes[v[i].mesh];
+    Inst& in = s.h_inst[i];
+    memset(&in, 0, sizeof(Inst));
+    long long F = r->n_faces;
+    int npf = (r->q + 1) * (r->q + 1);
+    in.nodes = m.nodes;
+    in.eaabb = m.box;
+    in.n_elem = m.n_elem;
+    in.p = m.p;
+    in.q = r->q;
+    in.n_faces = F;
+    if (r->on_device) {
+      in.faces_in = r->face_nodes;
+    } else {
+      double* stage = (double*)take(sizeof(double) * F * npf * 3);
+      CK(cudaMemcpyAsync(stage, r->face_nodes, sizeof(double) * F * npf * 3, cudaMemcpyHostToDevice, st));
+      in.faces_in = stage;
+    }
+    in.has_pose = r->pose ? 1 : 0;
+    if (r->pose) memcpy(in.pose, r->pose, sizeof(double) * 12);
+    in.surf = (double*)take(sizeof(double) * F * npf * 3);
+    in.fbox64 = (double*)take(sizeof(double) * F * 6);
+    in.fbox = (float*)take(sizeof(float) * F * 6);
+    in.fbin = (int*)take(sizeof(int) * F);
+    in.bin_faces = (int*)take(sizeof(int) * F);
+    in.cube = (uint8_t*)take(cube_bytes());
+    in.bin_cnt = (int*)take(sizeof(int) * nb);
+    in.bin_off = (int*)take(sizeof(int) * (nb + 1));
+    in.nbins_cap = nb;
+    in.tol = c->cfg.tol;
+    in.holemap_cells = c->cfg.holemap_cells;
+    in.bin_cubes = c->cfg.bin_cubes;
+    in.want_dist = r->dist_out ? 1 : 0;
+    for (int a = 0; a < 3; ++a) { in.sbox_key[a] = ~0ULL; in.sbox_key[3 + a] = 0ULL; }
+    s.h_off[i] = fo;
+    s.h_off[n + 1 + i] = eo;
+    fo += F;
+    eo += m.n_elem;
+  }
+  s.h_off[n] = fo;
+  s.h_off[2 * n + 1] = eo;
+  unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
+  unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
+  unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
+  int8_t* oflags = (int8_t*)take(ne_total);
+  double* odist = (double*)take(sizeof(double) * ne_total);
+  // outputs: caller's device buffers, or staging for host buffers
+  long long off = 0;
+  for (int i = 0; i < n; ++i) {
+    const dc_request* r = v[i].req;
+    Inst& in = s.h_inst[i];
+    if (r->on_device) {
+      in.flags = r->flags_out;
+      in.dist = r->dist_out;
+    } else {
+      in.flags = oflags + off;
+      in.dist = r->dist_out ? odist + off : nullptr;
+    }
+    off += in.n_elem;
+  }
+  (void)staged_out;
+
+  CK(cudaMemcpyAsync(d_inst, s.h_inst, sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_off, s.h_off, sizeof(long long) * 2 * (n + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(s.ring_ev[s.cur_ring], st));
+  s.ring_used[s.cur_ring] = true;
+  CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
+  const long long* foff = d_off;
+  const long long* eoff = d_off + n + 1;
+  const bool prof = c->cfg.profile != 0;
+  if (prof) CK(cudaEventRecord(s.ev[0], st));
+
+  const int TB = 256;
+  unsigned gf = (unsigned)((nf_total + TB - 1) / TB);
+  k_surface<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  k_grid<<<(n + 63) / 64, 64, 0, st>>>(d_inst, n);
+  k_clear<<<dim3(64, n), TB, 0, st>>>(d_inst);
+  k_tag<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  k_bin_scan<<<n, 1024, 0, st>>>(d_inst);
+  k_bin_fill<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  if (prof) CK(cudaEventRecord(s.ev[1], st));
+  const int cc_smem = c->cc_smem;
+  const int cc_cap = (cc_smem - (MAX_DIM * MAX_DIM + 1) * 4 - 64) / 8;
+  k_holemap_cc<<<n, 1024, cc_smem, st>>>(d_inst, cc_cap);
+  k_winding<<<dim3((unsigned)((max_tri + TB - 1) / TB), MAX_COMP, n), TB, 0, st>>>(d_inst);
+  if (prof) CK(cudaEventRecord(s.ev[2], st));
+  CandList cl{cand, (unsigned long long)ne_total, d_cnt};
+  CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
+  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl);
+  if (prof) CK(cudaEventRecord(s.ev[3], st));
+  const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
+  const int WPB = TB / 32;
+  if ((long long)Ld.total * WPB > c->smem_optin)
+    return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * WPB);
+  CandList none{redo, 0, d_cnt + 2};
+  if (c->cfg.precision == DC_FP32_RECHECK) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
+    occ = std::max(occ, 1);
+    k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
+    int occd = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
+    occd = std::max(occd, 1);
+    k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, rl, none, pmax, qmax, d_cnt + 4);
+  } else {
+    int occd = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
+    occd = std::max(occd, 1);
+    k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, cl, none, pmax, qmax, d_cnt + 4);
+  }
+  if (prof) CK(cudaEventRecord(s.ev[4], st));
+  CK(cudaGetLastError());
+  s.n_inst = n;
+  s.d_inst = d_inst;
+  s.d_cnt = d_cnt;
+  return DC_OK;
+}
+
+// copy results of a finished (synchronised) batch back and turn device error
+// bits into a status; fills ctx->last
+dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st) {
+  const int n = s.n_inst;
+  CK(cudaMemcpyAsync(s.h_cnt, s.d_cnt, sizeof(unsigned long long) * NCNT, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(s.h_inst, s.d_inst, sizeof(Inst) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  s.ring_used[s.cur_ring] = false;
+  dc_stats& S = c->last;
+  memset(&S, 0, sizeof(S));
+  int err = 0;
+  for (int i = 0; i < n; ++i) {
+    err |= s.h_inst[i].err;
+    S.n_elem += s.h_inst[i].n_elem;
+    S.holemap_components += s.h_inst[i].ncomp;
+  }
+  S.n_candidates = (int64_t)s.h_cnt[0];
+  S.faces_visited = (int64_t)s.h_cnt[4];
+  S.pairs_bulk = (int64_t)s.h_cnt[5];
+  S.pairs_recheck = (int64_t)s.h_cnt[6];
+  S.n_fringe = (int64_t)s.h_cnt[7];
+  S.fallbacks = (int64_t)s.h_cnt[10];
+  if (c->cfg.profile) {
+    cudaEventElapsedTime(&S.ms_surface, s.ev[0], s.ev[1]);
+    cudaEventElapsedTime(&S.ms_holemap, s.ev[1], s.ev[2]);
+    cudaEventElapsedTime(&S.ms_classify, s.ev[2], s.ev[3]);
+    cudaEventElapsedTime(&S.ms_exact, s.ev[3], s.ev[4]);
+    cudaEventElapsedTime(&S.ms_total, s.ev[0], s.ev[4]);
+  }
+  if (err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
+  if (err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");
+  if (err & (ERR_ROUNDS | ERR_RECHECK))
+    return fail(DC_EINTERNAL, "exact test capacity exceeded (error bits 0x%x)", err);
+  (void)v;
+  return DC_OK;
+}
+
+dc_status copy_out_host(Slot& s, const std::vector<InstReq>& v, cudaStream_t st) {
+  // host outputs: the kernels wrote into the arena staging area
+  long long off = 0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const dc_request* r = v[i].req;
+    long long ne = s.h_inst[i].n_elem;
+    if (!r->on_device) {
+      CK(cudaMemcpyAsync(r->flags_out, s.h_inst[i].flags, (size_t)ne, cudaMemcpyDeviceToHost, st));
+      if (r->dist_out) CK(cudaMemcpyAsync(r->dist_out, s.h_inst[i].dist, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
+    }
+    off += ne;
+  }
+  CK(cudaStreamSynchronize(st));
+  return DC_OK;
+}
+
+dc_status init_slot(Slot& s, int prof) {
+  CK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+  for (int r = 0; r < Slot::RING; ++r) CK(cudaEventCreateWithFlags(&s.ring_ev[r], cudaEventDisableTiming));
+  if (prof)
+    for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&s.ev[i]));
+  return DC_OK;
+}
+
+void free_slot(dc_ctx* c, Slot& s) {
+  if (s.stream) cudaStreamSynchronize(s.stream);
+  if (s.arena.base) { cudaFree(s.arena.base); c->arena_bytes -= s.arena.cap; }
+  for (int r = 0; r < Slot::RING; ++r) {
+    if (s.ring_inst[r]) cudaFreeHost(s.ring_inst[r]);
+    if (s.ring_off[r]) cudaFreeHost(s.ring_off[r]);
+    if (s.ring_ev[r]) cudaEventDestroy(s.ring_ev[r]);
+  }
+  if (s.h_cnt) cudaFreeHost(s.h_cnt);
+  if (s.h_flags) cudaFreeHost(s.h_flags);
+  if (s.h_dist) cudaFreeHost(s.h_dist);
+  for (int i = 0; i < 6; ++i)
+    if (s.ev[i]) cudaEventDestroy(s.ev[i]);
+  if (s.done) cudaEventDestroy(s.done);
+  if (s.stream) cudaStreamDestroy(s.stream);
+  s = Slot();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public ABI
+extern "C" {
+
+const char* dc_last_error(void) { return g_err.c_str(); }
+
+const char* dc_version(void) { return "directcut 0.1 (sm_103a)"; }
+
+dc_status dc_config_default(dc_config* cfg) {
+  if (!cfg) return fail(DC_EINVAL, "cfg is NULL");
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->precision = DC_FP32_RECHECK;
+  cfg->tol = 1e-7;
+  cfg->holemap_cells = 64;
+  cfg->bin_cubes = 4;
+  cfg->max_inflight = 4;
+  return DC_OK;
+}
+
+dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t n_meshes, dc_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(DC_EINVAL, "out is NULL");
+  *out = nullptr;
+  dc_config cfg;
+  if (cfg_in) cfg = *cfg_in; else dc_config_default(&cfg);
+  if (cfg.tol == 0.0) cfg.tol = 1e-7;
+  if (cfg.holemap_cells == 0) cfg.holemap_cells = 64;
+  if (cfg.bin_cubes == 0) cfg.bin_cubes = 4;
+  if (cfg.max_inflight == 0) cfg.max_inflight = 4;
+  if (!(cfg.tol > 0.0) || !std::isfinite(cfg.tol)) return fail(DC_EINVAL, "tol must be positive and finite");
+  if (cfg.holemap_cells < 8 || cfg.holemap_cells > MAX_CELLS) return fail(DC_EINVAL, "holemap_cells outside 8..%d", MAX_CELLS);
+  if (cfg.bin_cubes < 1 || cfg.bin_cubes > 16) return fail(DC_EINVAL, "bin_cubes outside 1..16");
+  if (cfg.max_inflight < 1 || cfg.max_inflight > 64) return fail(DC_EINVAL, "max_inflight outside 1..64");
+  if (cfg.precision != DC_FP64 && cfg.precision != DC_FP32_RECHECK) return fail(DC_EINVAL, "unknown precision %d", cfg.precision);
+  if (n_meshes < 1 || !meshes) return fail(DC_EINVAL, "at least one mesh is required");
+  for (int i = 0; i < n_meshes; ++i) {
+    const dc_mesh_desc& m = meshes[i];
+    if (m.p < 1 || m.p > MAX_P) return fail(DC_EINVAL, "mesh %d: order p=%d outside 1..%d", i, m.p, MAX_P);
+    if (m.n_elem < 1 || m.n_elem >= (1LL << 40)) return fail(DC_EINVAL, "mesh %d: n_elem=%lld out of range", i, (long long)m.n_elem);
+    if (!m.nodes) return fail(DC_EINVAL, "mesh %d: nodes is NULL", i);
+  }
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (cfg.device < 0 || cfg.device >= ndev) return fail(DC_EINVAL, "device %d not present (%d devices)", cfg.device, ndev);
+  CK(cudaSetDevice(cfg.device));
+  dc_ctx* c = new dc_ctx();
+  c->cfg = cfg;
+  auto bail = [&](dc_status st) { dc_destroy(c); return st; };
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaGetDeviceProperties failed"));
+  c->n_sm = prop.multiProcessorCount;
+  static unsigned char et[MAX_P][MAX_NTE][3], ft[MAX_Q][MAX_NTF][3];
+  build_tables(et, ft);
+  if (cudaMemcpyToSymbol(c_etri, et, sizeof(et)) != cudaSuccess || cudaMemcpyToSymbol(c_ftri, ft, sizeof(ft)) != cudaSuccess)
+    return bail(fail(DC_ECUDA, "uploading triangle tables failed"));
+  {
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_holemap_cc) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
+    c->cc_smem = (int)(c->smem_optin - fa.sharedSizeBytes) & ~255;
+    if (c->cc_smem < (MAX_DIM * MAX_DIM + 1) * 4 + 64 * 1024)
+      return bail(fail(DC_ECUDA, "device offers only %d bytes of shared memory per block", c->smem_optin));
+    cudaFuncAttributes fe, fd;
+    if (cudaFuncGetAttributes(&fe, k_exact<float>) != cudaSuccess || cudaFuncGetAttributes(&fd, k_exact<double>) != cudaSuccess)
+      return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
+    if (cudaFuncSetAttribute(k_holemap_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, c->cc_smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(c->smem_optin - fe.sharedSizeBytes)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(c->smem_optin - fd.sharedSizeBytes)) != cudaSuccess)
+      return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
+  }
+  c->slots.resize(cfg.max_inflight);
+  for (auto& s : c->slots) {
+    dc_status st = init_slot(s, cfg.profile);
+    if (st) return bail(st);
+  }
+  int* d_bad = nullptr;
+  if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  cudaStream_t st = c->slots[0].stream;
+  c->meshes.resize(n_meshes);
+  for (int i = 0; i < n_meshes; ++i) {
+    const dc_mesh_desc& md = meshes[i];
+    Mesh& m = c->meshes[i];
+    m.p = md.p;
+    m.n_elem = md.n_elem;
+    c->pmax = std::max(c->pmax, md.p);
+    size_t npe = (size_t)(md.p + 1) * (md.p + 1) * (md.p + 1);
+    size_t nb = sizeof(double) * npe * 3 * md.n_elem, bb = sizeof(float) * 6 * md.n_elem;
+    if (cfg.mem_budget_bytes && c->mesh_bytes + nb + bb > cfg.mem_budget_bytes) {
+      cudaFree(d_bad);
+      return bail(fail(DC_ENOMEM, "mesh %d does not fit the memory budget", i));
+    }
+    if (cudaMalloc(&m.nodes, nb) != cudaSuccess || cudaMalloc(&m.box, bb) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_bad);
+      return bail(fail(DC_ENOMEM, "mesh %d: cudaMalloc of %zu bytes failed", i, nb + bb));
+    }
+    c->mesh_bytes += nb + bb;
+    cudaMemcpyKind kind = md.nodes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(m.nodes, md.nodes, nb, kind, st) != cudaSuccess) {
+      cudaFree(d_bad);
+      return bail(fail(DC_ECUDA, "mesh %d: copying nodes failed", i));
+    }
+    cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+    k_elem_box<<<(unsigned)((md.n_elem + 255) / 256), 256, 0, st>>>(m.nodes, md.n_elem, (int)npe, m.box, d_bad);
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaFree(d_bad);
+      return bail(fail(DC_ECUDA, "mesh %d: element boxes failed: %s", i, cudaGetErrorString(cudaGetLastError())));
+    }
+    if (bad) {
+      cudaFree(d_bad);
+      return bail(fail(DC_EINVAL, "mesh %d has a NaN or infinite node", i));
+    }
+  }
+  cudaFree(d_bad);
+  *out = c;
+  return DC_OK;
+}
+
+static dc_status run_sync(dc_ctx* c, const std::vector<InstReq>& v, bool async_ok, cudaStream_t user) {
+  Slot& s = c->slots[0];
+  cudaStream_t st = user ? user : s.stream;
+  dc_status rc = enqueue(c, s, v, st, false);
+  if (rc) return rc;
+  if (async_ok) return DC_OK;
+  rc = finish(c, s, v, st);
+  dc_status rc2 = copy_out_host(s, v, st);
+  return rc ? rc : rc2;
+}
+
+dc_status dc_cut(dc_ctx* c, int32_t mesh, const dc_request* req) {
+  g_err.clear();
+  if (!c) return fail(DC_EINVAL, "ctx is NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  dc_status rc = validate_req(c, mesh, req);
+  if (rc) return rc;
+  if (req->async && !req->on_device) return fail(DC_EINVAL, "async requires device pointers");
+  CK(cudaSetDevice(c->cfg.device));
+  std::vector<InstReq> v{{mesh, req}};
+  return run_sync(c, v, req->async != 0, (cudaStream_t)req->stream);
+}
+
+dc_status dc_cut_batch(dc_ctx* c, int32_t n, const int32_t* meshes, const dc_request* reqs) {
+  g_err.clear();
+  if (!c) return fail(DC_EINVAL, "ctx is NULL");
+  if (n < 1 || !meshes || !reqs) return fail(DC_EINVAL, "empty batch");
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<InstReq> v;
+  v.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    dc_status rc = validate_req(c, meshes[i], &reqs[i]);
+    if (rc) return rc;
+    if (reqs[i].async) return fail(DC_EINVAL, "dc_cut_batch is synchronous; async must be 0");
+    v.push_back({meshes[i], &reqs[i]});
+  }
+  CK(cudaSetDevice(c->cfg.device));
+  return run_sync(c, v, false, (cudaStream_t)reqs[0].stream);
+}
+
+dc_status dc_get_stats(dc_ctx* c, dc_stats* out) {
+  if (!c || !out) return fail(DC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->last;
+  return DC_OK;
+}
+
+dc_status dc_submit(dc_ctx* c, int32_t mesh, const dc_request* req, uint64_t* ticket) {
+  g_err.clear();
+  if (!c || !ticket) return fail(DC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  dc_status rc = validate_req(c, mesh, req);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->cfg.device));
+  // slot 0 stays reserved for dc_cut; serving uses the others (or slot 0 when
+  // only one exists)
+  int pick = -1;
+  for (int i = (c->slots.size() > 1 ? 1 : 0); i < (int)c->slots.size(); ++i)
+    if (!c->slots[i].busy) { pick = i; break; }
+  if (pick < 0) return fail(DC_EBUSY, "all %zu serving slots are in flight", c->slots.size());
+  Slot& s = c->slots[pick];
+  std::vector<InstReq> v{{mesh, req}};
+  rc = enqueue(c, s, v, s.stream, true);
+  if (rc) return rc;
+  long long ne = c->meshes[mesh].n_elem;
+  s.host_out = !req->on_device;
+  s.user_flags = req->flags_out;
+  s.user_dist = req->dist_out;
+  s.out_n = ne;
+  if (s.host_out) {
+    CK(cudaMemcpyAsync(s.h_flags, s.h_inst[0].flags, (size_t)ne, cudaMemcpyDeviceToHost, s.stream));
+    if (req->dist_out) CK(cudaMemcpyAsync(s.h_dist, s.h_inst[0].dist, sizeof(double) * ne, cudaMemcpyDeviceToHost, s.stream));
+  }
+  CK(cudaMemcpyAsync(s.h_cnt, s.d_cnt, sizeof(unsigned long long) * NCNT, cudaMemcpyDeviceToHost, s.stream));
+  CK(cudaEventRecord(s.done, s.stream));
+  s.busy = true;
+  s.ticket = c->next_ticket++;
+  *ticket = s.ticket;
+  return DC_OK;
+}
+
+dc_status dc_poll(dc_ctx* c, uint64_t ticket, int64_t timeout_us) {
+  g_err.clear();
+  if (!c) return fail(DC_EINVAL, "ctx is NULL");
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      Slot* s = nullptr;
+      for (auto& x : c->slots)
+        if (x.busy && x.ticket == ticket) s = &x;
+      if (!s) return fail(DC_ENOTFOUND, "ticket %llu is not in flight", (unsigned long long)ticket);
+      cudaError_t q = cudaEventQuery(s->done);
+      if (q == cudaSuccess) {
+        std::vector<InstReq> none;
+        CK(cudaMemcpyAsync(s->h_inst, s->d_inst, sizeof(Inst) * s->n_inst, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        int err = 0;
+        for (int i = 0; i < s->n_inst; ++i) err |= s->h_inst[i].err;
+        if (s->host_out) {
+          memcpy(s->user_flags, s->h_flags, (size_t)s->out_n);
+          if (s->user_dist) memcpy(s->user_dist, s->h_dist, sizeof(double) * s->out_n);
+        }
+        s->busy = false;
+        if (err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
+        if (err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");
+        if (err & (ERR_ROUNDS | ERR_RECHECK)) return fail(DC_EINTERNAL, "exact test capacity exceeded (0x%x)", err);
+        return DC_OK;
+      }
+      if (q != cudaErrorNotReady) {
+        s->busy = false;
+        return fail(DC_ECUDA, "ticket %llu failed: %s", (unsigned long long)ticket, cudaGetErrorString(q));
+      }
+    }
+    auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_us >= 0 && el >= timeout_us) return DC_PENDING;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+void dc_destroy(dc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  for (auto& s : c->slots) free_slot(c, s);
+  for (auto& m : c->meshes) {
+    if (m.nodes) cudaFree(m.nodes);
+    if (m.box) cudaFree(m.box);
+  }
+  delete c;
+}
+
+}  // extern "C"

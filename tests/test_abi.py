@@ -1,0 +1,76 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports every
+function include/directcut.h declares, and the Python binding's structures
+match the header's layouts (checked by compiling the header with gcc)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1711_07663_gb300 as dc
+from paper_1711_07663_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "directcut.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return dc.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(dc_[a-z_]+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert set(names) == set(dc.EXPORTED), names
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", dc.lib_path()], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}$", out, flags=re.M), n
+
+
+def test_version_and_error_without_gpu(lib):
+    assert "sm_103a" in dc.dc_version()
+    assert isinstance(dc.dc_last_error(), str)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "directcut.h"\n'
+        "#define F(T, m) printf(#T \".\" #m \" %zu\\n\", offsetof(T, m))\n"
+        "#define S(T) printf(#T \" %zu\\n\", sizeof(T))\n"
+        "int main(void){\n"
+        "S(dc_mesh_desc); F(dc_mesh_desc,p); F(dc_mesh_desc,n_elem); F(dc_mesh_desc,nodes); F(dc_mesh_desc,nodes_on_device);\n"
+        "S(dc_config); F(dc_config,device); F(dc_config,precision); F(dc_config,mem_budget_bytes); F(dc_config,tol);\n"
+        "F(dc_config,holemap_cells); F(dc_config,bin_cubes); F(dc_config,max_inflight); F(dc_config,profile);\n"
+        "S(dc_request); F(dc_request,q); F(dc_request,n_faces); F(dc_request,face_nodes); F(dc_request,pose);\n"
+        "F(dc_request,flags_out); F(dc_request,dist_out); F(dc_request,on_device); F(dc_request,async); F(dc_request,stream);\n"
+        "S(dc_stats); F(dc_stats,holemap_components); F(dc_stats,ms_surface); F(dc_stats,ms_total);\n"
+        "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    rename = {"async": "async_"}
+    for cname, pyt in (("dc_mesh_desc", dc.dc_mesh_desc), ("dc_config", dc.dc_config), ("dc_request", dc.dc_request),
+                       ("dc_stats", dc.dc_stats)):
+        assert int(got[cname]) == ctypes.sizeof(pyt), cname
+        for key, val in got.items():
+            if key.startswith(cname + "."):
+                field = rename.get(key.split(".", 1)[1], key.split(".", 1)[1])
+                assert getattr(pyt, field).offset == int(val), key
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(dc, "_lib", None)
+    monkeypatch.setattr(dc, "lib_path", lambda: str(tmp_path / "absent.so"))
+    with pytest.raises(dc.DirectCutError):
+        dc.load()

@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 parallel direct cut.
+
+Workload (one step = one full cut, every phase of the hot path): background
+64^3 Q2 hexes (262,144 elements) on [-2,2]^3 curved by a sinusoidal node
+displacement of 0.1 h, cut by a dimpled sphere (336 Gaussian dimples, 6144 Q2
+faces).  The mesh is resident in HBM (created once); each step cuts it with
+the surface (1.33 MB of face nodes, already on the device for `value`).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  value = N_E * N_F / cut time (element-face
+relations resolved per second, summed over ranks); `e2e` is the same metric
+through the C ABI with host buffers (face upload and flag download inside the
+timed region); `roofline` is the FP32 exact-test kernel against the FP32 ALU
+peak; `cpu_baseline` is the CPU oracle on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cut ms & element-face tests/s at 64^3 Q2 hexes; p50/p99 cut latency, vs plain"
+UNIT = "element-face tests/s"
+WORKLOAD = "dimpled sphere (6144 Q2 faces, 336 dimples) cutting 64^3 Q2 hexes (262,144 elements, sinusoidal 0.1h)"
+# arithmetic of one triangle-pair evaluation (paper_1711_07663_gb300/csrc/flopcount.cu:
+# mean over near pairs; FMA = 2 flops)
+FLOPS_PER_PAIR = 936.5
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _scale64():
+    import workloads as W
+    return W.dimpled_sphere_case()
+
+
+def _mid32():
+    import workloads as W
+    return W.dimpled_sphere_case(n=32, m=16, seed=12)
+
+
+def _plain16():
+    import workloads as W
+    return W.sphere_in_box(n=16, p=2, m=8, q=2, seed=1)
+
+
+WORKLOADS = {"scale64": _scale64, "mid32": _mid32, "plain16": _plain16}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="scale64", choices=sorted(WORKLOADS),
+                    help="scale64 is the benchmark; the others are small cases for profiling")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as D
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    D.all_reduce(t, op=D.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as D
+        D.barrier()
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_sample(case, seconds, seed=0):
+    """Time the oracle (as it stands, all host cores) on random elements of the
+    workload until ~`seconds` of wall time; returns element-face tests/s."""
+    import oracle as O
+    g = np.random.default_rng(seed)
+    ncpu = os.cpu_count() or 1
+    done = 0
+    t0 = time.perf_counter()
+    batch = 64 * ncpu
+    while time.perf_counter() - t0 < seconds:
+        ids = g.choice(case.n_elem, size=batch, replace=False)
+        O.cut(case.p, case.nodes, case.q, case.faces, ids=ids)
+        done += batch
+    dt = time.perf_counter() - t0
+    return done * case.n_faces / dt, done, dt, ncpu
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    case = WORKLOADS[args.workload]()
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    vals = []
+    n_el = 0
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        cpu_oracle_sample(case, 0.5, seed=99)
+    for k in range(args.steps):
+        v, done, dt, ncpu = cpu_oracle_sample(case, per_step, seed=k)
+        vals.append(v)
+        n_el += done
+    value = float(np.mean(vals))
+    ms = case.n_elem * case.n_faces / value * 1e3
+    sample = f"{n_el} random elements of the workload (of {case.n_elem}), {args.steps} steps of ~{per_step:.1f} s"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "n_elem": case.n_elem,
+                                                         "n_faces": case.n_faces, "p": 2, "q": 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+    if world > 1:
+        import torch.distributed as D
+        D.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1711_07663_gb300 as dc
+    from paper_1711_07663_gb300 import build as B
+    import workloads as W
+
+    if rank == 0 or not os.path.exists(dc.lib_path()):
+        B.build()
+    barrier(world)
+    dc.load()
+    case = WORKLOADS[args.workload]()
+    NE, NF = case.n_elem, case.n_faces
+    nodes = torch.from_numpy(case.nodes).to(dev)
+    faces = torch.from_numpy(case.faces).to(dev)
+    flags = torch.empty(NE, dtype=torch.int8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    ctx = dc.Context([(case.p, nodes)], precision=dc.DC_FP32_RECHECK, profile=1, device=local)
+    for _ in range(args.warmup):
+        ctx.cut(0, case.q, faces, flags, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    exact_ms, redo_ms, bulk, rech, ncand, total_ms = [], [], [], [], [], []
+    surf_ms, hm_ms, cls_ms = [], [], []
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.6)
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)  # evict the previous step's data from L2 (untimed)
+        ev0[k].record(stream)
+        ctx.cut(0, case.q, faces, flags, stream=stream.cuda_stream)
+        ev1[k].record(stream)
+        st = ctx.stats()
+        exact_ms.append(st["ms_exact"])
+        redo_ms.append(st["ms_redo"])
+        bulk.append(st["pairs_bulk"])
+        rech.append(st["pairs_recheck"])
+        ncand.append(st["n_candidates"])
+        total_ms.append(st["ms_total"])
+        surf_ms.append(st["ms_surface"])
+        hm_ms.append(st["ms_holemap"])
+        cls_ms.append(st["ms_classify"])
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    t_sum = max_over_ranks(float(step_ms.sum()), world)
+    ms_per_step = t_sum / args.steps
+    value = world * NE * NF / (ms_per_step * 1e-3)
+
+    # plain single-instance FP64 path (same flags): "vs plain"
+    plain_ms = None
+    same_flags = None
+    f_plain = torch.empty_like(flags)
+    if args.plain_steps > 0:
+      with dc.Context([(case.p, nodes)], precision=dc.DC_FP64, device=local) as pctx:
+        pctx.cut(0, case.q, faces, f_plain, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        same_flags = bool(torch.equal(f_plain, flags))
+        pe = []
+        for k in range(args.plain_steps):
+            flush.fill_(k & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pctx.cut(0, case.q, faces, f_plain, stream=stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pe.append(a.elapsed_time(b))
+        plain_ms = float(np.median(pe))
+
+    # end to end through the public API with host buffers
+    faces_h = torch.from_numpy(case.faces).pin_memory()
+    flags_h = torch.empty(NE, dtype=torch.int8).pin_memory()
+    for _ in range(3):
+        ctx.cut(0, case.q, faces_h, flags_h)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.cut(0, case.q, faces_h, flags_h)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
+    e2e_same = bool(torch.equal(flags_h, flags.cpu()))
+
+    # roofline of the dominant kernel (FP32 exact test): ALU bound
+    ex_ms = float(np.mean(exact_ms))
+    pairs = float(np.mean(bulk))
+    achieved = pairs * FLOPS_PER_PAIR / (ex_ms * 1e-3) / 1e12
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, done, dt, ncpu = cpu_oracle_sample(case, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": ncpu, "kind": "oracle",
+               "sample": f"{done} random elements of the workload ({dt:.1f} s, all {ncpu} host threads)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.workload == "scale64" else args.workload, "n_elem": NE, "n_faces": NF, "p": 2, "q": 2,
+                       "precision": "fp32 bulk + fp64 re-solve", "mesh": "resident",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "cut_ms_p50": float(np.percentile(step_ms, 50)), "cut_ms_p99": float(np.percentile(step_ms, 99)),
+            "plain_fp64_ms": plain_ms, "speedup_vs_plain": (plain_ms / float(np.median(step_ms))) if plain_ms else None,
+            "plain_same_flags": same_flags,
+            "phases_ms": {"surface_bins": float(np.mean(surf_ms)), "holemap": float(np.mean(hm_ms)),
+                          "classify": float(np.mean(cls_ms)), "exact_fp32": ex_ms, "redo_fp64": float(np.mean(redo_ms)),
+                          "library_total": float(np.mean(total_ms))},
+            "candidates": int(np.mean(ncand)), "pairs_fp32": int(pairs), "pairs_fp64": int(np.mean(rech)),
+            "e2e": {"value": world * NE * NF / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                    "h2d_bytes_per_step": int(case.faces.nbytes), "d2h_bytes_per_step": int(NE), "same_flags": e2e_same},
+            "gpu_launches": 11 * args.steps,
+            "roofline": {"bound": "alu", "kernel": "k_exact<float>", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_per_unit": FLOPS_PER_PAIR, "units_per_launch": pairs,
+                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as D
+        D.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -120,7 +120,8 @@ typedef struct {
     float ms_surface;         /* profile=1 only: pose + face boxes + hole map tags + bins */
     float ms_holemap;         /* connected components + winding-number seeds */
     float ms_classify;        /* hole-map lookup + candidate compaction */
-    float ms_exact;           /* exact element-face tests + sign */
+    float ms_exact;           /* exact element-face tests + sign (main pass) */
+    float ms_redo;            /* FP64 pass over elements whose FP32 re-solve list overflowed */
     float ms_total;
 } dc_stats;
 

@@ -66,7 +66,8 @@ class dc_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_elem", "n_candidates", "n_fringe", "n_hole", "n_field",
                                              "faces_visited", "pairs_bulk", "pairs_recheck", "fallbacks",
                                              "holemap_components")] + \
-               [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_total")]
+               [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_redo",
+                                                  "ms_total")]
 
 
 _lib = None

@@ -416,6 +416,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
     occ = std::max(occ, 1);
     k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
+    if (prof) CK(cudaEventRecord(s.ev[5], st));
     int occd = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
     occd = std::max(occd, 1);
@@ -425,6 +426,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
     occd = std::max(occd, 1);
     k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, cl, none, pmax, qmax, d_cnt + 4);
+    if (prof) CK(cudaEventRecord(s.ev[5], st));
   }
   if (prof) CK(cudaEventRecord(s.ev[4], st));
   CK(cudaGetLastError());
@@ -460,7 +462,8 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
     cudaEventElapsedTime(&S.ms_surface, s.ev[0], s.ev[1]);
     cudaEventElapsedTime(&S.ms_holemap, s.ev[1], s.ev[2]);
     cudaEventElapsedTime(&S.ms_classify, s.ev[2], s.ev[3]);
-    cudaEventElapsedTime(&S.ms_exact, s.ev[3], s.ev[4]);
+    cudaEventElapsedTime(&S.ms_exact, s.ev[3], s.ev[5]);
+    cudaEventElapsedTime(&S.ms_redo, s.ev[5], s.ev[4]);
     cudaEventElapsedTime(&S.ms_total, s.ev[0], s.ev[4]);
   }
   if (err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");

@@ -379,7 +379,9 @@ __global__ void __launch_bounds__(1024) k_holemap_cc(Inst* __restrict__ I, int c
     unsigned d = desc[i];
     int r = run_row(d), y = r % ny, z = r / ny;
     bool border = run_x0(d) == 0 || (int)run_x1(d) == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
-    if (border) atomicOr(&desc[root], RUN_OUT);
+    // test first: the border runs all share one root, and serialised atomics
+    // on a single shared-memory word would dominate the kernel
+    if (border && !(((volatile unsigned*)desc)[root] & RUN_OUT)) atomicOr(&desc[root], RUN_OUT);
   }
   __syncthreads();
   // 6. number the enclosed components

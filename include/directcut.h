@@ -159,6 +159,44 @@ void dc_destroy(dc_ctx *ctx);
 /* Message for the calling thread's last failing call ("" if none). */
 const char *dc_last_error(void);
 
+/* Allocation-free cut, for callers that cannot allocate device memory at the
+ * time they cut: code running under CUDA stream capture (cudaMalloc cannot be
+ * captured), loops that forbid allocation after start-up, and hosts whose own
+ * allocator must own all device memory.  The paper has no counterpart; it is
+ * the cut of dc_cut for one background grid, without a context.
+ *
+ *   nodes       device pointer, [n_elem][(p+1)^3][3] float64 (not copied)
+ *   face_nodes  device pointer, [n_faces][(q+1)^2][3] float64
+ *   pose        host pointer to 12 doubles [R|t], or NULL
+ *   tol         fringe tolerance; 0 -> 1e-7
+ *   flags_out   device pointer, [n_elem] int8 (required)
+ *   dist_out    device pointer, [n_elem] float64, or NULL
+ *   stream      cudaStream_t to run on (NULL: the legacy default stream);
+ *               the call returns after that stream has finished the cut.
+ *
+ * Every scratch buffer comes from one fixed 8 MiB array in the library's
+ * device memory, which each GPU that loads the library holds until the
+ * process exits; the call makes no cudaMalloc/cudaFree (nor any other
+ * allocating call).  Sizes whose scratch does not fit are rejected with
+ * DC_EINVAL and a message giving the bytes needed (40 bytes per element, about
+ * 300 bytes per Q2 face or 700 per Q4 face, plus 0.7 MiB: 65,536 elements with
+ * 8,192 Q2 faces fit).  The hole map uses 64 cubes on the longest side and 4-cube
+ * face bins, the bulk tests FP32 with FP64 re-solve (flags identical to
+ * dc_cut).
+ *
+ * All calls in a process share the array, which keeps the last call's
+ * contents; each call resets what must start at zero.  Calls are serialised
+ * by a lock in the library; work on that array that overlapped on the GPU
+ * (another thread's stream running a call while a new one starts) would race,
+ * which the lock and the final stream synchronisation prevent.
+ *
+ * The first call on a device sets up (looks up the array's device address,
+ * uploads the triangle tables, sets kernel attributes) with that device
+ * current; make that first call before any stream capture begins. */
+dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double *nodes, int32_t q, int64_t n_faces,
+                         const double *face_nodes, const double *pose, double tol, int8_t *flags_out,
+                         double *dist_out, void *stream);
+
 /* Library version string. */
 const char *dc_version(void);
 

@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "DC_HOLE", "DC_FIELD", "DC_FRINGE", "DC_FP64", "DC_FP32_RECHECK", "DirectCutError", "load", "lib_path",
     "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
-    "dc_last_error", "dc_version", "Context", "EXPORTED",
+    "dc_last_error", "dc_version", "dc_cut_noalloc", "Context", "EXPORTED",
 ]
 
 DC_OK, DC_PENDING = 0, 1
@@ -30,7 +30,7 @@ DC_HOLE, DC_FIELD, DC_FRINGE = 0, 1, -1
 DC_FP64, DC_FP32_RECHECK = 0, 1
 
 EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
-            "dc_destroy", "dc_last_error", "dc_version")
+            "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = False):
         L.dc_last_error.restype = ctypes.c_char_p
         L.dc_version.argtypes = []
         L.dc_version.restype = ctypes.c_char_p
+        L.dc_cut_noalloc.argtypes = [i32, i64, P, i32, i64, P, P, ctypes.c_double, P, P, P]
+        L.dc_cut_noalloc.restype = i32
         _lib = L
         return L
 
@@ -226,6 +228,20 @@ def dc_get_stats(ctx) -> dict:
     s = dc_stats()
     _check(load().dc_get_stats(ctx, ctypes.byref(s)))
     return {n: getattr(s, n) for n, _ in dc_stats._fields_}
+
+
+def dc_cut_noalloc(p, nodes, q, faces, flags_out, dist_out=None, pose=None, tol=0.0, stream=None):
+    """Allocation-free cut (device tensors only): see dc_cut_noalloc in the header."""
+    np_, ndev, nk = _addr(nodes, np.float64)
+    fp, fdev, fk = _addr(faces, np.float64)
+    op, odev, ok = _addr(flags_out, np.int8)
+    dp, ddev, dk = _addr(dist_out, np.float64)
+    if not (ndev and fdev and odev and (dist_out is None or ddev)):
+        raise ValueError("dc_cut_noalloc takes device tensors only")
+    pk = None if pose is None else np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
+    _check(load().dc_cut_noalloc(int(p), int(nk.shape[0]), np_, int(q), int(fk.shape[0]), fp,
+                                 None if pk is None else pk.ctypes.data, float(tol), op, dp,
+                                 None if stream is None else int(stream)))
 
 
 def dc_destroy(ctx) -> None:

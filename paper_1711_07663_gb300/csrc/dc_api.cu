@@ -773,3 +773,169 @@ void dc_destroy(dc_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free cut
+// Some callers cannot allocate device memory when they cut: code that runs
+// while a stream is being captured into a CUDA graph (cudaMalloc is not a
+// capturable call), real-time loops that forbid allocation after start-up, and
+// hosts whose own allocator must own every device byte.  dc_cut_noalloc serves
+// them: the same cut as dc_cut, with every scratch buffer carved from the
+// fixed array below, which each GPU that loads this library holds until the
+// process exits.  In host code `g_noalloc_scratch` only names a host-side
+// stand-in for the symbol, never a device address: the address the kernels
+// get comes from cudaGetSymbolAddress, once per device, with that device
+// current.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+struct NoallocDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+  int n_sm = 0;
+  int smem_optin = 0;
+  int cc_smem = 0;
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+
+// first call on a device: symbol address, triangle tables, kernel attributes
+dc_status noalloc_setup(int dev, NoallocDevice& d) {
+  if (d.ready) return DC_OK;
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return fail(DC_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+  static unsigned char et[MAX_P][MAX_NTE][3], ft[MAX_Q][MAX_NTF][3];
+  build_tables(et, ft);
+  CK(cudaMemcpyToSymbol(c_etri, et, sizeof(et)));
+  CK(cudaMemcpyToSymbol(c_ftri, ft, sizeof(ft)));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  cudaFuncAttributes fa, fe, fd;
+  CK(cudaFuncGetAttributes(&fa, k_holemap_cc));
+  CK(cudaFuncGetAttributes(&fe, k_exact<float>));
+  CK(cudaFuncGetAttributes(&fd, k_exact<double>));
+  d.smem_optin = (int)prop.sharedMemPerBlockOptin;
+  d.cc_smem = (int)(d.smem_optin - fa.sharedSizeBytes) & ~255;
+  CK(cudaFuncSetAttribute(k_holemap_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, d.cc_smem));
+  CK(cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(d.smem_optin - fe.sharedSizeBytes)));
+  CK(cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(d.smem_optin - fd.sharedSizeBytes)));
+  d.n_sm = prop.multiProcessorCount;
+  d.scratch = (unsigned char*)ptr;
+  d.ready = true;
+  return DC_OK;
+}
+}  // namespace
+
+extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nodes, int32_t q, int64_t n_faces,
+                                    const double* face_nodes, const double* pose, double tol, int8_t* flags_out,
+                                    double* dist_out, void* stream) {
+  g_err.clear();
+  if (p < 1 || p > MAX_P) return fail(DC_EINVAL, "element order p=%d outside 1..%d", p, MAX_P);
+  if (q < 1 || q > MAX_Q) return fail(DC_EINVAL, "face order q=%d outside 1..%d", q, MAX_Q);
+  if (n_elem < 1 || n_faces < 1) return fail(DC_EINVAL, "n_elem and n_faces must be positive");
+  if (!nodes || !face_nodes || !flags_out) return fail(DC_EINVAL, "nodes, face_nodes and flags_out are required");
+  if (tol == 0.0) tol = 1e-7;
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DC_EINVAL, "tol must be positive and finite");
+  if (pose)
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(pose[i])) return fail(DC_EINVAL, "pose has a non-finite entry");
+  const int bin_cubes = 4, cells = 64;
+  const int nb = nbins_cap(bin_cubes);
+  const int npe = (p + 1) * (p + 1) * (p + 1), npf = (q + 1) * (q + 1);
+  // scratch plan (bytes, 256-aligned pieces)
+  size_t need = al256(sizeof(Inst)) + al256(sizeof(long long) * 4) + al256(sizeof(float) * 6 * n_elem) +
+                al256(sizeof(unsigned long long) * n_elem) * 2 + al256(sizeof(unsigned long long) * NCNT) +
+                al256(sizeof(double) * n_faces * npf * 3) + al256(sizeof(double) * n_faces * 6) +
+                al256(sizeof(float) * n_faces * 6) + al256(sizeof(int) * n_faces) * 2 + al256(cube_bytes()) +
+                al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) + al256(sizeof(int));
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return fail(DC_EINVAL, "dc_cut_noalloc: %lld elements (p=%d) and %lld faces (q=%d) need %zu bytes of scratch; "
+                "the fixed array holds %zu", (long long)n_elem, p, (long long)n_faces, q, need, NOALLOC_SCRATCH_BYTES);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(DC_EINVAL, "device ordinal %d not supported", dev);
+  NoallocDevice& D = g_noalloc_dev[dev];
+  dc_status rc = noalloc_setup(dev, D);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* pp = D.scratch;
+  auto take = [&](size_t bytes) { unsigned char* r = pp; pp += al256(bytes); return r; };
+  Inst* d_inst = (Inst*)take(sizeof(Inst));
+  long long* d_off = (long long*)take(sizeof(long long) * 4);
+  float* ebox = (float*)take(sizeof(float) * 6 * n_elem);
+  unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * n_elem);
+  unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * n_elem);
+  unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
+  Inst h;
+  memset(&h, 0, sizeof(h));
+  h.nodes = nodes;
+  h.eaabb = ebox;
+  h.n_elem = n_elem;
+  h.p = p;
+  h.faces_in = face_nodes;
+  h.n_faces = n_faces;
+  h.q = q;
+  h.has_pose = pose ? 1 : 0;
+  if (pose) memcpy(h.pose, pose, sizeof(double) * 12);
+  h.flags = flags_out;
+  h.dist = dist_out;
+  h.surf = (double*)take(sizeof(double) * n_faces * npf * 3);
+  h.fbox64 = (double*)take(sizeof(double) * n_faces * 6);
+  h.fbox = (float*)take(sizeof(float) * n_faces * 6);
+  h.fbin = (int*)take(sizeof(int) * n_faces);
+  h.bin_faces = (int*)take(sizeof(int) * n_faces);
+  h.cube = (uint8_t*)take(cube_bytes());
+  h.bin_cnt = (int*)take(sizeof(int) * nb);
+  h.bin_off = (int*)take(sizeof(int) * (nb + 1));
+  int* d_bad = (int*)take(sizeof(int));
+  h.nbins_cap = nb;
+  h.tol = tol;
+  h.holemap_cells = cells;
+  h.bin_cubes = bin_cubes;
+  h.want_dist = dist_out ? 1 : 0;
+  for (int a = 0; a < 3; ++a) { h.sbox_key[a] = ~0ULL; h.sbox_key[3 + a] = 0ULL; }
+  long long off[4] = {0, n_faces, 0, n_elem};
+  // the array keeps the previous call's contents: reset what must start at zero
+  CK(cudaMemcpyAsync(d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  const int TB = 256;
+  k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, d_bad);
+  unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
+  k_surface<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
+  k_grid<<<1, 64, 0, st>>>(d_inst, 1);
+  k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);
+  k_tag<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
+  k_bin_scan<<<1, 1024, 0, st>>>(d_inst);
+  k_bin_fill<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
+  const int cc_cap = (D.cc_smem - (MAX_DIM * MAX_DIM + 1) * 4 - 64) / 8;
+  k_holemap_cc<<<1, 1024, D.cc_smem, st>>>(d_inst, cc_cap);
+  long long ntri = n_faces * 2LL * q * q;
+  k_winding<<<dim3((unsigned)((ntri + TB - 1) / TB), MAX_COMP, 1), TB, 0, st>>>(d_inst);
+  CandList cl{cand, (unsigned long long)n_elem, d_cnt};
+  CandList rl{redo, (unsigned long long)n_elem, d_cnt + 2};
+  CandList none{redo, 0, d_cnt + 2};
+  k_classify<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(d_inst, d_off + 2, 1, n_elem, cl);
+  const ExLayout Lf = ex_layout(p, q, 4), Ld = ex_layout(p, q, 8);
+  const int WPB = TB / 32;
+  if ((long long)Ld.total * WPB > D.smem_optin)
+    return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", p, q, Ld.total * WPB);
+  int occ = 0, occd = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB));
+  k_exact<float><<<D.n_sm * std::max(occ, 1), TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, p, q, d_cnt + 4);
+  k_exact<double><<<D.n_sm * std::max(occd, 1), TB, (size_t)Ld.total * WPB, st>>>(d_inst, rl, none, p, q, d_cnt + 4);
+  CK(cudaGetLastError());
+  int bad = 0;
+  CK(cudaMemcpyAsync(&h, d_inst, sizeof(Inst), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return fail(DC_EINVAL, "an element node is NaN or infinite");
+  if (h.err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
+  if (h.err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");
+  if (h.err & (ERR_ROUNDS | ERR_RECHECK)) return fail(DC_EINTERNAL, "exact test capacity exceeded (error bits 0x%x)", h.err);
+  return DC_OK;
+}

@@ -179,7 +179,7 @@ const char *dc_last_error(void);
  * process exits; the call makes no cudaMalloc/cudaFree (nor any other
  * allocating call).  Sizes whose scratch does not fit are rejected with
  * DC_EINVAL and a message giving the bytes needed (40 bytes per element, about
- * 300 bytes per Q2 face or 700 per Q4 face, plus 0.7 MiB: 65,536 elements with
+ * 300 bytes per Q2 face or 700 per Q4 face, plus 2.4 MiB: 65,536 elements with
  * 8,192 Q2 faces fit).  The hole map uses 64 cubes on the longest side and 4-cube
  * face bins, the bulk tests FP32 with FP64 re-solve (flags identical to
  * dc_cut).

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -121,8 +122,34 @@ struct Arena {
   size_t cap = 0;
 };
 
+// Everything the kernel sequence of one cut depends on.  A slot keeps the
+// CUDA graphs it captured, keyed by these values; the per-request data (pose,
+// input/output pointers) lives in the instance table, which is copied to the
+// device before each launch, so one graph serves every request of a shape.
+struct LaunchParams {
+  int n = 0;
+  long long nf_total = 0, ne_total = 0, max_tri = 0;
+  int pmax = 1, qmax = 1, precision = 0, prof = 0;
+  Inst* d_inst = nullptr;
+  long long* d_off = nullptr;
+  unsigned long long *cand = nullptr, *redo = nullptr, *d_cnt = nullptr;
+  bool operator==(const LaunchParams& o) const {
+    return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && pmax == o.pmax &&
+           qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt;
+  }
+};
+
+struct GraphEntry {
+  LaunchParams key;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long last_use = 0;
+};
+
 struct Slot {
   cudaStream_t stream = nullptr;
+  std::vector<GraphEntry> graphs;   // captured launch sequences of this slot
+  unsigned long long use_clock = 0;
   cudaEvent_t done = nullptr;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   Arena arena;
@@ -171,8 +198,8 @@ struct dc_ctx {
   size_t arena_bytes = 0;
   dc_stats last{};
   int pmax = 1;
-  int cc_smem = 0;     // dynamic shared memory of the hole-map component kernel
   int smem_optin = 0;  // per-block opt-in shared memory limit of the device
+  bool use_graphs = true;  // replay captured launch sequences (DC_NO_GRAPHS=1 disables)
 };
 
 namespace {
@@ -191,6 +218,23 @@ int nbins_cap(int bin_cubes) {
 
 size_t cube_bytes() { return (size_t)MAX_DIM * MAX_DIM * CUBE_PITCH; }
 
+// hole-map run tables of one instance: counts, extents, parents, flags
+size_t run_bytes() {
+  const size_t rows = (size_t)MAX_DIM * MAX_DIM, slots = rows * RUNS_PER_ROW;
+  return al256(sizeof(int) * rows) + al256(sizeof(unsigned short) * slots) + al256(sizeof(int) * slots) +
+         al256(sizeof(unsigned) * slots) + 3 * al256(sizeof(int) * ROOT_CAP) +
+         al256(sizeof(int) * MAX_DIM * 2 * ZEDGE_CAP) + al256(sizeof(int) * MAX_DIM);
+}
+
+// the hole-map component kernels over every row of every instance
+void launch_components(Inst* d_inst, int n, cudaStream_t st) {
+  dim3 g((MAX_DIM * MAX_DIM + 255) / 256, n);
+  k_runs<<<g, 256, 0, st>>>(d_inst);
+  k_slice_cc<<<dim3(MAX_DIM, n), 256, 0, st>>>(d_inst);
+  k_join_cc<<<n, 1024, 0, st>>>(d_inst);
+  k_run_states<<<g, 256, 0, st>>>(d_inst);
+}
+
 // bytes of arena a batch needs
 size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
   size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
@@ -200,7 +244,8 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
     int npf = (r.req->q + 1) * (r.req->q + 1);
     if (!r.req->on_device) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
     s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(double) * F * 6) + al256(sizeof(float) * F * 6) +
-         al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1));
+         al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) +
+         run_bytes();
   }
   s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
   s += al256(sizeof(unsigned long long) * NCNT);
@@ -219,6 +264,8 @@ dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
   }
   if (s.arena.base) {
     CK(cudaStreamSynchronize(s.stream));
+    for (auto& g : s.graphs) cudaGraphExecDestroy(g.exec);
+    s.graphs.clear();
     CK(cudaFree(s.arena.base));
     c->arena_bytes -= s.arena.cap;
     s.arena.base = nullptr;
@@ -291,6 +338,97 @@ dc_status validate_req(dc_ctx* c, int mesh, const dc_request* r) {
   return DC_OK;
 }
 
+// Phase events: inside a stream capture they must become event-record nodes.
+cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+}
+
+// The kernel sequence of one (batched) cut on stream st.
+dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st, bool capturing) {
+  const int n = P.n;
+  const long long nf_total = P.nf_total, ne_total = P.ne_total, max_tri = P.max_tri;
+  const int pmax = P.pmax, qmax = P.qmax;
+  Inst* d_inst = P.d_inst;
+  long long* d_off = P.d_off;
+  unsigned long long *cand = P.cand, *redo = P.redo, *d_cnt = P.d_cnt;
+  CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
+  const long long* foff = d_off;
+  const long long* eoff = d_off + n + 1;
+  const bool prof = P.prof != 0;
+  if (prof) CK(record(s.ev[0], st, capturing));
+
+  const int TB = 256;
+  unsigned gf = (unsigned)((nf_total + TB - 1) / TB);
+  k_surface<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  k_grid<<<(n + 63) / 64, 64, 0, st>>>(d_inst, n);
+  k_clear<<<dim3(64, n), TB, 0, st>>>(d_inst);
+  k_tag<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  k_bin_scan<<<n, 1024, 0, st>>>(d_inst);
+  k_bin_fill<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  if (prof) CK(record(s.ev[1], st, capturing));
+  launch_components(d_inst, n, st);
+  k_winding<<<dim3((unsigned)((max_tri + TB - 1) / TB), MAX_COMP, n), TB, 0, st>>>(d_inst);
+  if (prof) CK(record(s.ev[2], st, capturing));
+  CandList cl{cand, (unsigned long long)ne_total, d_cnt};
+  CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
+  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl);
+  if (prof) CK(record(s.ev[3], st, capturing));
+  const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
+  const int WPB = TB / 32;
+  if ((long long)Ld.total * WPB > c->smem_optin)
+    return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * WPB);
+  CandList none{redo, 0, d_cnt + 2};
+  if (P.precision == DC_FP32_RECHECK) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
+    occ = std::max(occ, 1);
+    k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
+    if (prof) CK(record(s.ev[5], st, capturing));
+    // the FP64 redo pass is rarely non-empty: a small persistent grid keeps
+    // its launch cheap
+    k_exact<double><<<std::min(c->n_sm, 16), TB, (size_t)Ld.total * WPB, st>>>(d_inst, rl, none, pmax, qmax, d_cnt + 4);
+  } else {
+    int occd = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
+    occd = std::max(occd, 1);
+    k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, cl, none, pmax, qmax, d_cnt + 4);
+    if (prof) CK(record(s.ev[5], st, capturing));
+  }
+  if (prof) CK(record(s.ev[4], st, capturing));
+  return DC_OK;
+}
+
+// Replay (capturing on first use) the graph of this launch shape.
+dc_status launch_graph(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st) {
+  GraphEntry* hit = nullptr;
+  for (auto& g : s.graphs)
+    if (g.key == P) hit = &g;
+  if (!hit) {
+    if (s.graphs.size() >= 8) {
+      auto lru = std::min_element(s.graphs.begin(), s.graphs.end(),
+                                  [](const GraphEntry& a, const GraphEntry& b) { return a.last_use < b.last_use; });
+      cudaGraphExecDestroy(lru->exec);
+      s.graphs.erase(lru);
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+    dc_status rc = launch_cut(c, s, P, s.stream, true);
+    cudaError_t ec = cudaStreamEndCapture(s.stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ec != cudaSuccess) return fail(DC_ECUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+    GraphEntry e;
+    e.key = P;
+    cudaError_t ei = cudaGraphInstantiate(&e.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(DC_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ei));
+    s.graphs.push_back(e);
+    hit = &s.graphs.back();
+  }
+  hit->last_use = ++s.use_clock;
+  CK(cudaGraphLaunch(hit->exec, st));
+  return DC_OK;
+}
+
 // Enqueue the whole cut of a batch on slot s (no host synchronisation).
 dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool staged_out) {
   const int n = (int)v.size();
@@ -345,6 +483,18 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.bin_cnt = (int*)take(sizeof(int) * nb);
     in.bin_off = (int*)take(sizeof(int) * (nb + 1));
     in.nbins_cap = nb;
+    {
+      const size_t rows = (size_t)MAX_DIM * MAX_DIM, slots = rows * RUNS_PER_ROW;
+      in.run_cnt = (int*)take(sizeof(int) * rows);
+      in.run_xx = (unsigned short*)take(sizeof(unsigned short) * slots);
+      in.run_par = (int*)take(sizeof(int) * slots);
+      in.run_flag = (unsigned*)take(sizeof(unsigned) * slots);
+      in.root_info = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
+      in.root_slot = (int*)take(sizeof(int) * ROOT_CAP);
+      in.root_label = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
+      in.zedge = (int*)take(sizeof(int) * MAX_DIM * 2 * ZEDGE_CAP);
+      in.zedge_cnt = (int*)take(sizeof(int) * MAX_DIM);
+    }
     in.tol = c->cfg.tol;
     in.holemap_cells = c->cfg.holemap_cells;
     in.bin_cubes = c->cfg.bin_cubes;
@@ -382,53 +532,17 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   CK(cudaMemcpyAsync(d_off, s.h_off, sizeof(long long) * 2 * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(s.ring_ev[s.cur_ring], st));
   s.ring_used[s.cur_ring] = true;
-  CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
-  const long long* foff = d_off;
-  const long long* eoff = d_off + n + 1;
-  const bool prof = c->cfg.profile != 0;
-  if (prof) CK(cudaEventRecord(s.ev[0], st));
-
-  const int TB = 256;
-  unsigned gf = (unsigned)((nf_total + TB - 1) / TB);
-  k_surface<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
-  k_grid<<<(n + 63) / 64, 64, 0, st>>>(d_inst, n);
-  k_clear<<<dim3(64, n), TB, 0, st>>>(d_inst);
-  k_tag<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
-  k_bin_scan<<<n, 1024, 0, st>>>(d_inst);
-  k_bin_fill<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
-  if (prof) CK(cudaEventRecord(s.ev[1], st));
-  const int cc_smem = c->cc_smem;
-  const int cc_cap = (cc_smem - (MAX_DIM * MAX_DIM + 1) * 4 - 64) / 8;
-  k_holemap_cc<<<n, 1024, cc_smem, st>>>(d_inst, cc_cap);
-  k_winding<<<dim3((unsigned)((max_tri + TB - 1) / TB), MAX_COMP, n), TB, 0, st>>>(d_inst);
-  if (prof) CK(cudaEventRecord(s.ev[2], st));
-  CandList cl{cand, (unsigned long long)ne_total, d_cnt};
-  CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
-  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl);
-  if (prof) CK(cudaEventRecord(s.ev[3], st));
-  const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
-  const int WPB = TB / 32;
-  if ((long long)Ld.total * WPB > c->smem_optin)
-    return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * WPB);
-  CandList none{redo, 0, d_cnt + 2};
-  if (c->cfg.precision == DC_FP32_RECHECK) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
-    occ = std::max(occ, 1);
-    k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
-    if (prof) CK(cudaEventRecord(s.ev[5], st));
-    int occd = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
-    occd = std::max(occd, 1);
-    k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, rl, none, pmax, qmax, d_cnt + 4);
-  } else {
-    int occd = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
-    occd = std::max(occd, 1);
-    k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, cl, none, pmax, qmax, d_cnt + 4);
-    if (prof) CK(cudaEventRecord(s.ev[5], st));
+  LaunchParams lp;
+  lp.n = n; lp.nf_total = nf_total; lp.ne_total = ne_total; lp.max_tri = max_tri;
+  lp.pmax = pmax; lp.qmax = qmax; lp.precision = c->cfg.precision; lp.prof = c->cfg.profile != 0;
+  lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt;
+  {
+    const ExLayout Ld = ex_layout(pmax, qmax, 8);
+    if ((long long)Ld.total * (256 / 32) > c->smem_optin)
+      return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * 8);
   }
-  if (prof) CK(cudaEventRecord(s.ev[4], st));
+  dc_status lrc = c->use_graphs ? launch_graph(c, s, lp, st) : launch_cut(c, s, lp, st, false);
+  if (lrc) return lrc;
   CK(cudaGetLastError());
   s.n_inst = n;
   s.d_inst = d_inst;
@@ -501,6 +615,8 @@ dc_status init_slot(Slot& s, int prof) {
 
 void free_slot(dc_ctx* c, Slot& s) {
   if (s.stream) cudaStreamSynchronize(s.stream);
+  for (auto& g : s.graphs) cudaGraphExecDestroy(g.exec);
+  s.graphs.clear();
   if (s.arena.base) { cudaFree(s.arena.base); c->arena_bytes -= s.arena.cap; }
   for (int r = 0; r < Slot::RING; ++r) {
     if (s.ring_inst[r]) cudaFreeHost(s.ring_inst[r]);
@@ -566,6 +682,10 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
   CK(cudaSetDevice(cfg.device));
   dc_ctx* c = new dc_ctx();
   c->cfg = cfg;
+  {
+    const char* ng = getenv("DC_NO_GRAPHS");
+    c->use_graphs = !(ng && ng[0] == '1');
+  }
   auto bail = [&](dc_status st) { dc_destroy(c); return st; };
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaGetDeviceProperties failed"));
@@ -576,16 +696,10 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     return bail(fail(DC_ECUDA, "uploading triangle tables failed"));
   {
     c->smem_optin = prop.sharedMemPerBlockOptin;
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_holemap_cc) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
-    c->cc_smem = (int)(c->smem_optin - fa.sharedSizeBytes) & ~255;
-    if (c->cc_smem < (MAX_DIM * MAX_DIM + 1) * 4 + 64 * 1024)
-      return bail(fail(DC_ECUDA, "device offers only %d bytes of shared memory per block", c->smem_optin));
     cudaFuncAttributes fe, fd;
     if (cudaFuncGetAttributes(&fe, k_exact<float>) != cudaSuccess || cudaFuncGetAttributes(&fd, k_exact<double>) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
-    if (cudaFuncSetAttribute(k_holemap_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, c->cc_smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fe.sharedSizeBytes)) != cudaSuccess ||
         cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fd.sharedSizeBytes)) != cudaSuccess)
@@ -794,7 +908,6 @@ struct NoallocDevice {
   unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
   int n_sm = 0;
   int smem_optin = 0;
-  int cc_smem = 0;
 };
 std::mutex g_noalloc_mu;
 NoallocDevice g_noalloc_dev[64];
@@ -811,13 +924,10 @@ dc_status noalloc_setup(int dev, NoallocDevice& d) {
   CK(cudaMemcpyToSymbol(c_ftri, ft, sizeof(ft)));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, dev));
-  cudaFuncAttributes fa, fe, fd;
-  CK(cudaFuncGetAttributes(&fa, k_holemap_cc));
+  cudaFuncAttributes fe, fd;
   CK(cudaFuncGetAttributes(&fe, k_exact<float>));
   CK(cudaFuncGetAttributes(&fd, k_exact<double>));
   d.smem_optin = (int)prop.sharedMemPerBlockOptin;
-  d.cc_smem = (int)(d.smem_optin - fa.sharedSizeBytes) & ~255;
-  CK(cudaFuncSetAttribute(k_holemap_cc, cudaFuncAttributeMaxDynamicSharedMemorySize, d.cc_smem));
   CK(cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(d.smem_optin - fe.sharedSizeBytes)));
   CK(cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(d.smem_optin - fd.sharedSizeBytes)));
   d.n_sm = prop.multiProcessorCount;
@@ -848,7 +958,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
                 al256(sizeof(unsigned long long) * n_elem) * 2 + al256(sizeof(unsigned long long) * NCNT) +
                 al256(sizeof(double) * n_faces * npf * 3) + al256(sizeof(double) * n_faces * 6) +
                 al256(sizeof(float) * n_faces * 6) + al256(sizeof(int) * n_faces) * 2 + al256(cube_bytes()) +
-                al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) + al256(sizeof(int));
+                al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) + run_bytes() + al256(sizeof(int));
   if (need > NOALLOC_SCRATCH_BYTES)
     return fail(DC_EINVAL, "dc_cut_noalloc: %lld elements (p=%d) and %lld faces (q=%d) need %zu bytes of scratch; "
                 "the fixed array holds %zu", (long long)n_elem, p, (long long)n_faces, q, need, NOALLOC_SCRATCH_BYTES);
@@ -889,6 +999,18 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   h.cube = (uint8_t*)take(cube_bytes());
   h.bin_cnt = (int*)take(sizeof(int) * nb);
   h.bin_off = (int*)take(sizeof(int) * (nb + 1));
+  {
+      const size_t rows = (size_t)MAX_DIM * MAX_DIM, slots = rows * RUNS_PER_ROW;
+      h.run_cnt = (int*)take(sizeof(int) * rows);
+      h.run_xx = (unsigned short*)take(sizeof(unsigned short) * slots);
+      h.run_par = (int*)take(sizeof(int) * slots);
+      h.run_flag = (unsigned*)take(sizeof(unsigned) * slots);
+      h.root_info = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
+      h.root_slot = (int*)take(sizeof(int) * ROOT_CAP);
+      h.root_label = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
+      h.zedge = (int*)take(sizeof(int) * MAX_DIM * 2 * ZEDGE_CAP);
+      h.zedge_cnt = (int*)take(sizeof(int) * MAX_DIM);
+    }
   int* d_bad = (int*)take(sizeof(int));
   h.nbins_cap = nb;
   h.tol = tol;
@@ -911,8 +1033,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   k_tag<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
   k_bin_scan<<<1, 1024, 0, st>>>(d_inst);
   k_bin_fill<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
-  const int cc_cap = (D.cc_smem - (MAX_DIM * MAX_DIM + 1) * 4 - 64) / 8;
-  k_holemap_cc<<<1, 1024, D.cc_smem, st>>>(d_inst, cc_cap);
+  launch_components(d_inst, 1, st);
   long long ntri = n_faces * 2LL * q * q;
   k_winding<<<dim3((unsigned)((ntri + TB - 1) / TB), MAX_COMP, 1), TB, 0, st>>>(d_inst);
   CandList cl{cand, (unsigned long long)n_elem, d_cnt};

@@ -18,6 +18,10 @@ constexpr int MAX_NTF = 2 * MAX_Q * MAX_Q;                        // triangles p
 constexpr int MAX_CELLS = 80;                                     // hole-map cubes, longest side
 constexpr int MAX_DIM = MAX_CELLS + 2;                            // + one padding cube per side
 constexpr int MAX_COMP = 4;   // enclosed hole-map components resolved by a winding number
+constexpr int RUNS_PER_ROW = 24;  // run slots per hole-map row (a row with more is made NEAR)
+constexpr int ROOTS_PER_SLICE = 48;                       // slice components (more: the map degrades to NEAR)
+constexpr int ROOT_CAP = ROOTS_PER_SLICE * (MAX_CELLS + 2); // compact root ids, ROOTS_PER_SLICE per slice
+constexpr int ZEDGE_CAP = 512;    // distinct (root, lower run) joins between a slice and the one below
 
 // hole-map cube states (Sec. 4.2 hole maps, after the 0/1 flip):
 //   OUT  = reached from the border, outside the surface
@@ -63,6 +67,16 @@ struct Inst {
   int* bin_off;            // [nbins + 1]
   int* bin_faces;          // [n_faces]
   int nbins_cap;
+  int* run_cnt;            // hole-map runs per row [rows]
+  unsigned short* run_xx;  // run extents x0 | x1 << 8 [rows][RUNS_PER_ROW]
+  int* run_par;            // union-find parents [rows][RUNS_PER_ROW]
+  unsigned* run_flag;      // compact id of each slice-root slot [rows][RUNS_PER_ROW]
+  unsigned* root_info;     // per compact root: border bit [ROOT_CAP]
+  int* root_slot;          // per compact root: its slot [ROOT_CAP]
+  unsigned* root_label;    // per compact root: final label [ROOT_CAP]
+  int* zedge;              // per slice: (root id, slot of the joined root below) pairs [MAX_DIM][2*ZEDGE_CAP]
+  int* zedge_cnt;          // per slice [MAX_DIM]
+  int nroots;              // unused (kept for the layout of older tools)
   // parameters
   double tol;
   int holemap_cells;
@@ -76,6 +90,8 @@ struct Inst {
   int dims[3];
   double bs;
   int bdims[3];
+  float origin_f[3];               // float copies for the bulk lookups (margins cover
+  float inv_ds_f, inv_bs_f;        // their rounding)
   int ncomp;
   int comp_seed[MAX_COMP];
   float comp_w[MAX_COMP];

@@ -646,17 +646,19 @@ __device__ __noinline__ int side_of(const Inst& in, int q, const double* o, cons
   return best_sign;
 }
 
-// hole-map label of a point: 1 inside, 2 outside, 0 undecided (a NEAR cube,
-// or an enclosed component whose winding number is not near 0 or 1)
-__device__ __forceinline__ int point_label(const Inst& in, double x, double y, double z) {
-  double c[3] = {(x - in.origin[0]) / in.ds, (y - in.origin[1]) / in.ds, (z - in.origin[2]) / in.ds};
+// hole-map label of a point: 1 inside, 2 outside, 0 undecided (near a cube
+// face, in a NEAR cube, or in an enclosed component whose winding number is
+// not near 0 or 1).  Float arithmetic; `m` (in cube units) covers its rounding.
+__device__ __forceinline__ int point_label(const Inst& in, float x, float y, float z, float m) {
+  float c[3] = {(x - in.origin_f[0]) * in.inv_ds_f, (y - in.origin_f[1]) * in.inv_ds_f,
+                (z - in.origin_f[2]) * in.inv_ds_f};
   int ix[3];
   for (int a = 0; a < 3; ++a) {
-    if (!(c[a] >= 0.0) || !(c[a] < (double)in.dims[a])) return 2;  // outside the map: outside the surface box
-    ix[a] = (int)c[a];
-    // a point on a cube face belongs to both cubes: require a clear interior
-    double fr = c[a] - ix[a];
-    if (fr < 1e-6 || fr > 1.0 - 1e-6) return 0;
+    if (c[a] < -m || c[a] > (float)in.dims[a] + m) return 2;  // outside the map: outside the surface box
+    float fl = floorf(c[a]);
+    if (c[a] - fl < m || fl + 1.0f - c[a] < m) return 0;      // too close to a cube face
+    ix[a] = (int)fl;
+    if (ix[a] < 0 || ix[a] >= in.dims[a]) return 0;
   }
   uint8_t s = in.cube[((long long)ix[2] * in.dims[1] + ix[1]) * CUBE_PITCH + ix[0]];
   if (s == CUBE_OUT) return 2;
@@ -680,9 +682,13 @@ __device__ void gather_round(WarpCtx<T>& W, WarpState<T>& S, double r, const flo
   for (int a = 0; a < 6; ++a) gmax = fmaxf(gmax, fabsf(W.gbox[a]));
   const float ecx = 0.5f * (W.gbox[0] + W.gbox[3]), ecy = 0.5f * (W.gbox[1] + W.gbox[4]), ecz = 0.5f * (W.gbox[2] + W.gbox[5]);
   for (int a = 0; a < 3; ++a) {
-    double glo = (double)W.gbox[a] - r - (double)fext[a], ghi = (double)W.gbox[3 + a] + r;
-    b0[a] = clampi(cube_floor((glo - in.origin[a]) / in.bs - 1e-6, in.bdims[a]), 0, in.bdims[a] - 1);
-    b1[a] = clampi(cube_floor((ghi - in.origin[a]) / in.bs + 1e-6, in.bdims[a]), 0, in.bdims[a] - 1);
+    // float bin range, widened by 1e-3 bin plus the rounding of its inputs
+    float rf = (float)r * 1.0001f;
+    float glo = W.gbox[a] - rf - fext[a], ghi = W.gbox[3 + a] + rf;
+    float o = in.origin_f[a];
+    float slack = 1e-3f + 16.0f * 5.9604645e-8f * (fabsf(glo) + fabsf(ghi) + fabsf(o)) * in.inv_bs_f;
+    b0[a] = clampi(cube_floor((double)((glo - o) * in.inv_bs_f - slack), in.bdims[a]), 0, in.bdims[a] - 1);
+    b1[a] = clampi(cube_floor((double)((ghi - o) * in.inv_bs_f + slack), in.bdims[a]), 0, in.bdims[a] - 1);
   }
   for (int bz = b0[2]; bz <= b1[2] && !S.fringe_done; ++bz)
     for (int by = b0[1]; by <= b1[1] && !S.fringe_done; ++by)
@@ -751,9 +757,16 @@ __device__ bool process_element(WarpCtx<T>& W, WarpState<T>& S, ExCounters& cnt)
   smax = warp_max(smax);
   if (lane == 0) W.Se = smax;
   __syncwarp();
-  // side labels of the element's nodes from the hole map
+  // side labels of the element's nodes from the hole map (node = frame
+  // origin + local coordinate, in float; margin in cube units for rounding)
   int lab_or = 0;
-  for (int nd = lane; nd < W.npe; nd += 32) lab_or |= point_label(in, en[3 * nd], en[3 * nd + 1], en[3 * nd + 2]);
+  {
+    const float ox = (float)W.o[0], oy = (float)W.o[1], oz = (float)W.o[2];
+    const float gm = fmaxf(fmaxf(fabsf(ox), fabsf(oy)), fabsf(oz)) + (float)smax;
+    const float m = 1e-5f + 16.0f * 5.9604645e-8f * gm * in.inv_ds_f;
+    for (int nd = lane; nd < W.npe; nd += 32)
+      lab_or |= point_label(in, ox + (float)W.ex[nd], oy + (float)W.ey[nd], oz + (float)W.ez[nd], m);
+  }
   const bool any_in = __any_sync(FULL, lab_or & 1), any_out = __any_sync(FULL, lab_or & 2);
   int8_t flag;
   double dist = 0.0;

@@ -124,6 +124,9 @@ __global__ void k_grid(Inst* __restrict__ I, int n_inst) {
     nb *= in.bdims[a];
   }
   in.bs = ds * in.bin_cubes;
+  for (int a = 0; a < 3; ++a) in.origin_f[a] = (float)in.origin[a];
+  in.inv_ds_f = (float)(1.0 / ds);
+  in.inv_bs_f = (float)(1.0 / in.bs);
   if (nb > in.nbins_cap) in.err |= ERR_DEGENERATE;  // sized on the host for the worst case
 }
 
@@ -155,14 +158,18 @@ __global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, 
   Inst& in = I[ii];
   if (in.err & ERR_DEGENERATE) return;
   long long f = g - foff[ii];
-  const double ds = in.ds;
-  const double mu = 2.0 * in.tol + 1e-9 * ds;  // fringe margin, with room for rounding
+  // cube range of the face box inflated by the fringe margin 2 tol, in float:
+  // the extra 1e-3 cube (plus 16 ulp of the coordinates) only ever adds cubes
+  const float mu = (float)(2.0 * in.tol);
   int c0[3], c1[3], b[3];
   for (int a = 0; a < 3; ++a) {
-    double lo = in.fbox64[6 * f + a], hi = in.fbox64[6 * f + 3 + a];
-    c0[a] = max(cube_floor((lo - mu - in.origin[a]) / ds - 1e-6, in.dims[a]), 0);
-    c1[a] = min(cube_floor((hi + mu - in.origin[a]) / ds + 1e-6, in.dims[a]), in.dims[a] - 1);
-    b[a] = clampi(cube_floor((lo - in.origin[a]) / in.bs, in.bdims[a]), 0, in.bdims[a] - 1);
+    float lo = in.fbox[6 * f + a], hi = in.fbox[6 * f + 3 + a];  // rounded outward
+    float o = in.origin_f[a];
+    float slack = 1e-3f + 16.0f * 5.9604645e-8f * (fabsf(lo) + fabsf(hi) + fabsf(o)) * in.inv_ds_f;
+    float x0 = (lo - mu - o) * in.inv_ds_f - slack, x1 = (hi + mu - o) * in.inv_ds_f + slack;
+    c0[a] = max(cube_floor((double)x0, in.dims[a]), 0);
+    c1[a] = min(cube_floor((double)x1, in.dims[a]), in.dims[a] - 1);
+    b[a] = clampi(cube_floor((double)((lo - o) * in.inv_bs_f), in.bdims[a]), 0, in.bdims[a] - 1);
   }
   for (int z = c0[2]; z <= c1[2]; ++z)
     for (int y = c0[1]; y <= c1[1]; ++y) {
@@ -216,12 +223,13 @@ __global__ void k_bin_fill(Inst* __restrict__ I, const long long* __restrict__ f
 }
 
 // ------------------------------------------------------------------ a3: components
-// Run descriptor: x1 bits 0-6, x0 bits 7-13, row bits 14-26; flags in 27-31.
-constexpr unsigned RUN_OUT = 1u << 31, RUN_UNKNOWN = 1u << 30;
-__device__ __forceinline__ unsigned run_x1(unsigned d) { return d & 127u; }
-__device__ __forceinline__ unsigned run_x0(unsigned d) { return (d >> 7) & 127u; }
-__device__ __forceinline__ unsigned run_row(unsigned d) { return (d >> 14) & 8191u; }
-__device__ __forceinline__ unsigned run_comp(unsigned d) { return (d >> 27) & 7u; }
+// The non-NEAR cubes of each x-row form runs; runs of face-adjacent rows that
+// overlap in x are connected.  Five small kernels over all rows of all
+// instances: runs into fixed per-row slots, union-find in global memory
+// (hooks by atomicCAS at L2, larger root onto smaller, so parents always point
+// to smaller slots and finds terminate), flatten + mark the components that
+// touch the map border (outside), number the enclosed ones, write the states.
+constexpr unsigned RUN_OUT = 1u, RUN_UNKNOWN = 2u;  // run_flag bits; component id in bits 4..
 
 __device__ __forceinline__ void row_mask(const uint8_t* row, int nx, unsigned long long& m0, unsigned long long& m1) {
   // bit x set when cube x of the row is not NEAR
@@ -245,12 +253,58 @@ __device__ __forceinline__ void row_mask(const uint8_t* row, int nx, unsigned lo
   }
 }
 
-__device__ __forceinline__ bool mbit(unsigned long long m0, unsigned long long m1, int x) {
-  return x < 64 ? ((m0 >> x) & 1ull) : ((m1 >> (x - 64)) & 1ull);
+// first set bit at or after x of the 128-bit mask (m0 low word), or 128
+__device__ __forceinline__ int next_set(unsigned long long m0, unsigned long long m1, int x) {
+  if (x < 64) {
+    unsigned long long t = m0 & (~0ull << x);
+    if (t) return __ffsll((long long)t) - 1;
+    return m1 ? 64 + __ffsll((long long)m1) - 1 : 128;
+  }
+  if (x >= 128) return 128;
+  unsigned long long t = m1 & (~0ull << (x - 64));
+  return t ? 64 + __ffsll((long long)t) - 1 : 128;
 }
 
+__device__ __forceinline__ int rows_of(const Inst& in) { return in.dims[1] * in.dims[2]; }
+
+// 1. runs of each row into slots (grid.y = instance)
+__global__ void k_runs(Inst* __restrict__ I) {
+  Inst& in = I[blockIdx.y];
+  if (in.err & ERR_DEGENERATE) return;
+  const int nx = in.dims[0], nrows = rows_of(in);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    unsigned long long m0, m1;
+    uint8_t* row = in.cube + (long long)r * CUBE_PITCH;
+    row_mask(row, nx, m0, m1);
+    int n = 0, x = 0;
+    bool over = false;
+    while (true) {
+      int x0 = next_set(m0, m1, x);
+      if (x0 >= nx) break;
+      int x1 = min(next_set(~m0, ~m1, x0), nx) - 1;
+      if (n == RUNS_PER_ROW) { over = true; break; }
+      int sl = r * RUNS_PER_ROW + n;
+      in.run_xx[sl] = (unsigned short)(x0 | (x1 << 8));
+      ++n;
+      x = x1 + 1;
+    }
+    if (over) {
+      // too many runs: make the row NEAR (walls only split components, and
+      // every enclosed component is labelled by its winding number)
+      for (int k = 0; k < nx; ++k) row[k] = CUBE_NEAR;
+      n = 0;
+    }
+    in.run_cnt[r] = n;
+  }
+}
+
+__device__ __forceinline__ bool overlap(unsigned short a, unsigned short b) {
+  return (int)(a & 0xff) <= (int)(b >> 8) && (int)(b & 0xff) <= (int)(a >> 8);
+}
+
+// union-find over shared-memory parents that always point to smaller slots
+// (path halving; hooks by atomicCAS of the larger root onto the smaller)
 __device__ int uf_find(volatile int* parent, int i) {
-  // path halving; parents always point to smaller indices, so this terminates
   int p = parent[i];
   while (p != i) {
     int gp = parent[p];
@@ -258,6 +312,15 @@ __device__ int uf_find(volatile int* parent, int i) {
     i = p;
     p = parent[i];
   }
+  return i;
+}
+
+// root walk without writes: compression must first read every root this
+// way, then (after a barrier) store them, because a concurrent path-splitting
+// write could otherwise replace a stored root by an intermediate ancestor
+__device__ __forceinline__ int uf_root(const volatile int* parent, int i) {
+  int p;
+  while ((p = parent[i]) != i) i = p;
   return i;
 }
 
@@ -271,143 +334,261 @@ __device__ void uf_union(volatile int* parent, int a, int b) {
   }
 }
 
-// One CTA per instance.  Dynamic shared memory: row offsets, run descriptors
-// and union-find parents for up to `cap` runs.
-__global__ void __launch_bounds__(1024) k_holemap_cc(Inst* __restrict__ I, int cap) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_total, s_ncomp;
-  Inst& in = I[blockIdx.x];
+// 2. components inside each z-slice, in shared memory (one CTA per slice and
+//    instance).  Runs of rows y and y-1 that overlap are joined; every run
+//    records its slice root (the smallest slot of its slice component) in
+//    run_par, every slice root gets a compact id (run_flag of the root slot),
+//    its border bit and slot.  Each distinct (root of slice z, run of slice
+//    z-1) overlap is emitted once; the join resolves the lower run's root.
+// Labels of the runs of one slice by log-depth merging: in round w, the row
+// blocks [2kw, 2kw+w) and [2kw+w, 2kw+2w) are joined across their boundary
+// rows (every boundary y >= 1 is joined in exactly one round, w = its lowest
+// set bit), one thread per boundary; then every run is relinked to its root
+// (read all roots, barrier, write), so the trees stay flat and no find walks
+// a chain.  One row per thread: ny <= blockDim.  Ends with parents = roots =
+// the smallest slot of each component.
+__device__ void slice_label(volatile int* par, const unsigned short* xx, const unsigned char* cnt, int ny) {
+  const int y = threadIdx.x;
+  const int n = y < ny ? cnt[y] : 0;
+  for (int w = 1; w < ny; w <<= 1) {
+    // boundary rows of this round: y = (2k+1) w
+    if (y < ny && y >= w && ((y / w) & 1) && (y % w) == 0) {
+      const int m = cnt[y - 1];
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < m; ++j)
+          if (overlap(xx[y * RUNS_PER_ROW + k], xx[(y - 1) * RUNS_PER_ROW + j]))
+            uf_union(par, y * RUNS_PER_ROW + k, (y - 1) * RUNS_PER_ROW + j);
+    }
+    __syncthreads();
+    int rr[RUNS_PER_ROW];
+    for (int k = 0; k < n; ++k) rr[k] = uf_root(par, y * RUNS_PER_ROW + k);
+    __syncthreads();
+    for (int k = 0; k < n; ++k) par[y * RUNS_PER_ROW + k] = rr[k];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_slice_cc(Inst* __restrict__ I) {
+  constexpr int SL = MAX_DIM * RUNS_PER_ROW;
+  __shared__ int par[SL];
+  __shared__ unsigned short xx[SL], xxd[SL];
+  __shared__ unsigned char cnt[MAX_DIM], cntd[MAX_DIM];
+  __shared__ unsigned bord[SL];
+  constexpr int HB = 2 * ZEDGE_CAP;                 // hash buckets for the distinct joins
+  __shared__ unsigned long long ekeys[HB];
+  __shared__ int s_ne, s_full, s_nloc;
+  Inst& in = I[blockIdx.y];
   if (in.err & ERR_DEGENERATE) return;
   const int nx = in.dims[0], ny = in.dims[1], nz = in.dims[2];
-  const int nrows = ny * nz;
-  int* row_off = reinterpret_cast<int*>(smem);
-  unsigned* desc = reinterpret_cast<unsigned*>(row_off + MAX_DIM * MAX_DIM + 1);
-  volatile int* parent = reinterpret_cast<volatile int*>(desc + cap);
-  const int tid = threadIdx.x, T = blockDim.x;
-
-  // 1. runs per row
-  for (int r = tid; r < nrows; r += T) {
-    unsigned long long m0, m1;
-    row_mask(in.cube + (long long)r * CUBE_PITCH, nx, m0, m1);
-    unsigned long long s0 = m0 & ~(m0 << 1);
-    unsigned long long s1 = m1 & ~((m1 << 1) | (m0 >> 63));
-    row_off[r] = __popcll(s0) + __popcll(s1);
+  const int z = blockIdx.x;
+  if (z >= nz) return;
+  const int r0 = z * ny, rd0 = (z - 1) * ny;
+  if (threadIdx.x == 0) { s_ne = 0; s_full = 0; s_nloc = 0; }
+  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+    cnt[y] = (unsigned char)in.run_cnt[r0 + y];
+    cntd[y] = z > 0 ? (unsigned char)in.run_cnt[rd0 + y] : 0;
+  }
+  // the set of joins starts empty: shared memory may still hold keys of an
+  // earlier block (the same slice of another instance has the same slots)
+  for (int t = threadIdx.x; t < HB; t += blockDim.x) ekeys[t] = ~0ull;
+  for (int k = threadIdx.x; k < ny * RUNS_PER_ROW; k += blockDim.x) {
+    par[k] = k;
+    bord[k] = 0u;
+    xx[k] = in.run_xx[r0 * RUNS_PER_ROW + k];
+    xxd[k] = z > 0 ? in.run_xx[rd0 * RUNS_PER_ROW + k] : 0;
   }
   __syncthreads();
-  // 2. exclusive scan of row counts (chunked; T threads)
-  {
-    int chunk = (nrows + T - 1) / T;
-    int r0 = min(tid * chunk, nrows), r1 = min(r0 + chunk, nrows);
-    int s = 0;
-    for (int r = r0; r < r1; ++r) s += row_off[r];
-    // block scan of s via warp shuffles
-    __shared__ int wsum[32];
-    int lane = tid & 31, w = tid >> 5;
-    int v = s;
-    for (int o = 1; o < 32; o <<= 1) {
-      int u = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += u;
+  static_assert(MAX_DIM <= 256, "one row per thread");
+  slice_label(par, xx, cnt, ny);
+  // border bits of the slice roots; root slots, ids
+  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+    const int n = cnt[y];
+    for (int k = 0; k < n; ++k) {
+      const int sl = y * RUNS_PER_ROW + k;
+      unsigned short a = xx[sl];
+      bool b = y == 0 || y == ny - 1 || z == 0 || z == nz - 1 || (a & 0xff) == 0 || (int)(a >> 8) == nx - 1;
+      if (b && !(((volatile unsigned*)bord)[par[sl]] & 1u)) atomicOr(&bord[par[sl]], 1u);
+      in.run_par[(r0 + y) * RUNS_PER_ROW + k] = r0 * RUNS_PER_ROW + par[sl];
     }
-    if (lane == 31) wsum[w] = v;
-    __syncthreads();
-    if (w == 0) {
-      int x = (lane < (T >> 5)) ? wsum[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += u;
+  }
+  __syncthreads();
+  // compact ids of this slice's roots: the range [z R, z R + R), R = ROOTS_PER_SLICE
+  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+    const int n = cnt[y];
+    for (int k = 0; k < n; ++k) {
+      const int sl = y * RUNS_PER_ROW + k;
+      if (par[sl] != sl) continue;
+      int loc = atomicAdd(&s_nloc, 1);
+      if (loc >= ROOTS_PER_SLICE) continue;
+      const int id = z * ROOTS_PER_SLICE + loc;
+      const int gs = r0 * RUNS_PER_ROW + sl;
+      in.run_flag[gs] = (unsigned)id;
+      in.root_info[id] = bord[sl];
+      in.root_slot[id] = gs;
+    }
+  }
+  __syncthreads();
+  for (int t = s_nloc + threadIdx.x; t < ROOTS_PER_SLICE; t += blockDim.x) in.root_slot[z * ROOTS_PER_SLICE + t] = -1;
+  // distinct joins with slice z-1: key = (root slot here, root slot below)
+  if (z > 0) {
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+      const int n = cnt[y], m = cntd[y];
+      for (int k = 0; k < n; ++k) {
+        const int sl = y * RUNS_PER_ROW + k;
+        for (int j = 0; j < m; ++j) {
+          const int sd = y * RUNS_PER_ROW + j;
+          if (!overlap(xx[sl], xxd[sd])) continue;
+          unsigned long long key = ((unsigned long long)(r0 * RUNS_PER_ROW + par[sl]) << 32) |
+                                   (unsigned)(rd0 * RUNS_PER_ROW + sd);
+          // shared hash set, open addressing, bounded probing
+          unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (HB - 1);
+          bool done = false;
+          for (int probe = 0; probe < HB && !done; ++probe) {
+            unsigned long long old = atomicCAS(&ekeys[h], ~0ull, key);
+            done = (old == ~0ull || old == key);
+            h = (h + 1) & (HB - 1);
+          }
+          if (!done) s_full = 1;
+        }
       }
-      wsum[lane] = x;
     }
-    __syncthreads();
-    int excl = v - s + (w ? wsum[w - 1] : 0);
-    __syncthreads();
-    int run = excl;
-    for (int r = r0; r < r1; ++r) {
-      int c = row_off[r];
-      row_off[r] = run;
-      run += c;
-    }
-    if (tid == T - 1) { row_off[nrows] = run; s_total = run; s_ncomp = 0; }
   }
   __syncthreads();
-  const int R = s_total;
-  if (R > cap) {
-    // Too many runs for the table: degrade every undecided cube to NEAR.
-    // The classification stays exact (those elements take the exact test).
-    if (tid == 0) { in.err |= ERR_RUNS; in.ncomp = 0; }
-    for (int r = tid; r < nrows; r += T) {
+  for (int t = threadIdx.x; t < HB; t += blockDim.x) {
+    unsigned long long k = ekeys[t];
+    if (k == ~0ull) continue;
+    int pos = atomicAdd(&s_ne, 1);
+    if (pos < ZEDGE_CAP) {
+      in.zedge[z * 2 * ZEDGE_CAP + 2 * pos] = (int)(k >> 32);
+      in.zedge[z * 2 * ZEDGE_CAP + 2 * pos + 1] = (int)(k & 0xffffffffu);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_nloc > ROOTS_PER_SLICE) atomicOr(&in.err, (int)ERR_RUNS);
+    if (s_full || s_ne > ZEDGE_CAP) {
+      atomicOr(&in.err, (int)ERR_RUNS);  // the join degrades the map to NEAR: still exact
+      in.zedge_cnt[z] = 0;
+    } else {
+      in.zedge_cnt[z] = s_ne;
+    }
+  }
+}
+
+// 3. join the slices (one CTA per instance, shared memory over the compact
+//    slice roots): components with a border run are outside; the others are
+//    numbered (at most MAX_COMP get a winding-number seed); each compact root
+//    receives its final label.
+__global__ void __launch_bounds__(1024) k_join_cc(Inst* __restrict__ I) {
+  __shared__ int par[ROOT_CAP];
+  __shared__ unsigned flag[ROOT_CAP];
+  __shared__ int eoff[MAX_DIM + 1];
+  __shared__ int s_ncomp;
+  Inst& in = I[blockIdx.x];
+  if (in.err & ERR_DEGENERATE) return;
+  const int nz = in.dims[2];
+  const int nroots = nz * ROOTS_PER_SLICE;
+  if (in.err & ERR_RUNS) {
+    // too many slice components for the tables: every undecided cube becomes
+    // NEAR (exact: those elements take the exact test)
+    const int nx = in.dims[0], nrows = in.dims[1] * nz;
+    if (threadIdx.x == 0) { in.err |= ERR_RUNS; in.ncomp = 0; }
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      in.run_cnt[r] = 0;
       uint8_t* row = in.cube + (long long)r * CUBE_PITCH;
       for (int x = 0; x < nx; ++x) row[x] = CUBE_NEAR;
     }
     return;
   }
-  // 3. run table
-  for (int r = tid; r < nrows; r += T) {
-    unsigned long long m0, m1;
-    row_mask(in.cube + (long long)r * CUBE_PITCH, nx, m0, m1);
-    int k = row_off[r];
-    int x = 0;
-    while (x < nx) {
-      if (!mbit(m0, m1, x)) { ++x; continue; }
-      int x0 = x;
-      while (x < nx && mbit(m0, m1, x)) ++x;
-      desc[k] = ((unsigned)r << 14) | ((unsigned)x0 << 7) | (unsigned)(x - 1);
-      parent[k] = k;
-      ++k;
+  if (threadIdx.x == 0) s_ncomp = 0;
+  for (int i = threadIdx.x; i < nroots; i += blockDim.x) {
+    par[i] = i;
+    // ids a slice did not use are marked outside so they are never numbered
+    flag[i] = (in.root_slot[i] < 0 || in.root_info[i]) ? RUN_OUT : 0u;
+  }
+  // per-slice edge counts (parallel loads), then their prefix from shared memory
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) eoff[z + 1] = z ? in.zedge_cnt[z] : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    eoff[0] = 0;
+    for (int z = 1; z <= nz; ++z) eoff[z] += eoff[z - 1];
+  }
+  __syncthreads();
+  // edges of all slices, flattened over the threads
+  for (int e = threadIdx.x; e < eoff[nz]; e += blockDim.x) {
+    int lo = 0, hi = nz - 1;
+    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (eoff[mid] <= e) lo = mid; else hi = mid - 1; }
+    const int z = lo, t = e - eoff[z];
+    // a: root slot of the run above; b: slot of the run below, whose slice
+    // root the lower slice recorded in run_par
+    int a = (int)in.run_flag[in.zedge[z * 2 * ZEDGE_CAP + 2 * t]];
+    int b = (int)in.run_flag[in.run_par[in.zedge[z * 2 * ZEDGE_CAP + 2 * t + 1]]];
+    uf_union(par, a, b);
+  }
+  __syncthreads();
+  {
+    // two-phase compression (ROOT_CAP <= 4 * blockDim)
+    static_assert(ROOT_CAP <= 4 * 1024, "four roots per thread");  // 48 x 82 = 3936
+    int rr[4];
+    for (int m = 0; m < 4; ++m) {
+      int i = threadIdx.x + m * blockDim.x;
+      rr[m] = i < nroots ? uf_root(par, i) : 0;
+    }
+    __syncthreads();
+    for (int m = 0; m < 4; ++m) {
+      int i = threadIdx.x + m * blockDim.x;
+      if (i >= nroots) continue;
+      par[i] = rr[m];
+      if ((flag[i] & RUN_OUT) && !(((volatile unsigned*)flag)[rr[m]] & RUN_OUT)) atomicOr(&flag[rr[m]], RUN_OUT);
     }
   }
   __syncthreads();
-  // 4. union face-adjacent runs (rows y+1 and z+1)
-  for (int i = tid; i < R; i += T) {
-    unsigned d = desc[i];
-    int r = run_row(d), x0 = run_x0(d), x1 = run_x1(d);
-    int y = r % ny, z = r / ny;
-    int nbr[2] = {(y + 1 < ny) ? r + 1 : -1, (z + 1 < nz) ? r + ny : -1};
-    for (int t = 0; t < 2; ++t) {
-      if (nbr[t] < 0) continue;
-      for (int j = row_off[nbr[t]]; j < row_off[nbr[t] + 1]; ++j) {
-        unsigned e = desc[j];
-        if ((int)run_x0(e) <= x1 && (int)run_x1(e) >= x0) uf_union(parent, i, j);
+  for (int i = threadIdx.x; i < nroots; i += blockDim.x) {
+    if (par[i] != i || (flag[i] & RUN_OUT)) continue;
+    int c = atomicAdd(&s_ncomp, 1);
+    if (c < MAX_COMP) {
+      flag[i] |= (unsigned)c << 4;
+      int gs = in.root_slot[i];
+      in.comp_seed[c] = (gs / RUNS_PER_ROW) * CUBE_PITCH + (in.run_xx[gs] & 0xff);
+    } else {
+      flag[i] |= RUN_UNKNOWN;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nroots; i += blockDim.x) in.root_label[i] = flag[par[i]];
+  if (threadIdx.x == 0) in.ncomp = s_ncomp;
+}
+
+// 5. cube states of each row from its runs (16-byte stores)
+__global__ void k_run_states(Inst* __restrict__ I) {
+  Inst& in = I[blockIdx.y];
+  if (in.err & ERR_DEGENERATE) return;
+  const int nrows = rows_of(in);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    const int n = in.run_cnt[r];
+    if (!n) continue;  // all NEAR (or a row made NEAR in step 1)
+    unsigned w[CUBE_PITCH / 4];
+#pragma unroll
+    for (int i = 0; i < CUBE_PITCH / 4; ++i) w[i] = 0x02020202u;
+    for (int k = 0; k < n; ++k) {
+      int sl = r * RUNS_PER_ROW + k;
+      unsigned fl = in.root_label[in.run_flag[in.run_par[sl]]];
+      unsigned v = (fl & RUN_OUT) ? CUBE_OUT : ((fl & RUN_UNKNOWN) ? CUBE_NEAR : (CUBE_COMP0 + (fl >> 4)));
+      unsigned short xx = in.run_xx[sl];
+      int x0 = xx & 0xff, x1 = xx >> 8;
+#pragma unroll
+      for (int i = 0; i < CUBE_PITCH / 4; ++i) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int x = 4 * i + b;
+          if (x >= x0 && x <= x1) w[i] = (w[i] & ~(0xffu << (8 * b))) | (v << (8 * b));
+        }
       }
     }
+    uint4* row4 = reinterpret_cast<uint4*>(in.cube + (long long)r * CUBE_PITCH);
+#pragma unroll
+    for (int i = 0; i < CUBE_PITCH / 16; ++i) row4[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
   }
-  __syncthreads();
-  // 5. compress; components that touch the map border are outside
-  for (int i = tid; i < R; i += T) {
-    int root = uf_find(parent, i);
-    parent[i] = root;
-    unsigned d = desc[i];
-    int r = run_row(d), y = r % ny, z = r / ny;
-    bool border = run_x0(d) == 0 || (int)run_x1(d) == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
-    // test first: the border runs all share one root, and serialised atomics
-    // on a single shared-memory word would dominate the kernel
-    if (border && !(((volatile unsigned*)desc)[root] & RUN_OUT)) atomicOr(&desc[root], RUN_OUT);
-  }
-  __syncthreads();
-  // 6. number the enclosed components
-  for (int i = tid; i < R; i += T) {
-    if (parent[i] == i && !(desc[i] & RUN_OUT)) {
-      int k = atomicAdd(&s_ncomp, 1);
-      if (k < MAX_COMP) {
-        atomicOr(&desc[i], (unsigned)k << 27);
-        unsigned d = desc[i];
-        in.comp_seed[k] = (int)(run_row(d) * CUBE_PITCH + run_x0(d));
-        in.comp_w[k] = 0.0f;
-      } else {
-        atomicOr(&desc[i], RUN_UNKNOWN);
-      }
-    }
-  }
-  __syncthreads();
-  // 7. write the states
-  for (int i = tid; i < R; i += T) {
-    unsigned d = desc[i];
-    unsigned rd = desc[parent[i]];
-    uint8_t st = (rd & RUN_OUT) ? CUBE_OUT : ((rd & RUN_UNKNOWN) ? CUBE_NEAR : (uint8_t)(CUBE_COMP0 + run_comp(rd)));
-    uint8_t* row = in.cube + (long long)run_row(d) * CUBE_PITCH;
-    for (int x = run_x0(d); x <= (int)run_x1(d); ++x) row[x] = st;
-  }
-  if (tid == 0) in.ncomp = min(s_ncomp, MAX_COMP);
 }
 
 // winding number of each enclosed component's seed cube centre (FP32 solid
@@ -416,7 +597,7 @@ __global__ void __launch_bounds__(1024) k_holemap_cc(Inst* __restrict__ I, int c
 __global__ void k_winding(Inst* __restrict__ I) {
   Inst& in = I[blockIdx.z];
   const int k = blockIdx.y;
-  if (k >= in.ncomp || (in.err & ERR_DEGENERATE)) return;
+  if (k >= min(in.ncomp, MAX_COMP) || (in.err & ERR_DEGENERATE)) return;
   const int q = in.q, ntf = 2 * q * q, npf = (q + 1) * (q + 1);
   long long ntri = in.n_faces * ntf;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -117,3 +117,24 @@ def test_memory_budget_admission():
         with pytest.raises(dc.DirectCutError) as ei:
             ctx.cut(0, c.q, c.faces)
         assert ei.value.status == dc.DC_EBUSY
+
+
+def test_graph_replay_equals_direct_launches(monkeypatch):
+    """Cuts replayed from captured CUDA graphs equal directly launched cuts,
+    across repeated requests of one shape and a change of shape."""
+    cases = [W.sphere_in_box(n=10, p=2, m=6, q=2, seed=41), W.sphere_in_box(n=10, p=2, m=4, q=2, seed=42)]
+    outs = {}
+    for mode in ("graphs", "direct"):
+        if mode == "direct":
+            monkeypatch.setenv("DC_NO_GRAPHS", "1")
+        with dc.Context([(cases[0].p, cases[0].nodes)]) as ctx:
+            res = []
+            for cs in (cases[0], cases[1], cases[0], cases[0]):
+                f = np.empty(cs.n_elem, dtype=np.int8)
+                d = np.empty(cs.n_elem)
+                ctx.cut(0, cs.q, cs.faces, f, d)
+                res.append((f, d))
+            outs[mode] = res
+    for (f1, d1), (f2, d2) in zip(outs["graphs"], outs["direct"]):
+        assert np.array_equal(f1, f2) and np.array_equal(d1, d2)
+    assert np.array_equal(outs["graphs"][0][0], outs["graphs"][2][0])

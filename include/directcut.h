@@ -123,6 +123,12 @@ typedef struct {
     float ms_exact;           /* exact element-face tests + sign (main pass) */
     float ms_redo;            /* FP64 pass over elements whose FP32 re-solve list overflowed */
     float ms_total;
+    int64_t near_tasks;       /* flags-only requests: (element, face) pairs of boxes within
+                                 tol listed for the flat exact test */
+    int64_t n_full_search;    /* candidates decided by the full per-element search
+                                 (distances requested, or no node labelled by the hole map) */
+    int64_t near_pairs_full;  /* flags-only requests: listed triangle pairs that plane
+                                 separation could not settle (full FP32 test) */
 } dc_stats;
 
 /* Fill *cfg with the defaults listed above. */

@@ -67,7 +67,8 @@ class dc_stats(ctypes.Structure):
                                              "faces_visited", "pairs_bulk", "pairs_recheck", "fallbacks",
                                              "holemap_components")] + \
                [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_redo",
-                                                  "ms_total")]
+                                                  "ms_total")] + \
+               [(n, ctypes.c_int64) for n in ("near_tasks", "n_full_search", "near_pairs_full")]
 
 
 _lib = None

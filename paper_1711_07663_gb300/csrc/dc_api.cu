@@ -20,7 +20,7 @@
 #include <vector>
 
 #include "../../include/directcut.h"
-#include "dc_exact.cuh"
+#include "dc_near.cuh"
 
 using namespace dc;
 
@@ -45,8 +45,11 @@ dc_status fail(dc_status st, const char* fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------------------ element boxes
+// Node boxes rounded outward and, when loc/org are given, the element frame of
+// the exact test: origin at the centre of the float box, node coordinates
+// relative to it rounded to float (the values every exact-test kernel uses).
 __global__ void k_elem_box(const double* __restrict__ nodes, long long n_elem, int npe, float* __restrict__ box,
-                           int* __restrict__ bad) {
+                           float* __restrict__ loc, double* __restrict__ org, int* __restrict__ bad) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_elem) return;
   const double* x = nodes + e * npe * 3;
@@ -59,11 +62,18 @@ __global__ void k_elem_box(const double* __restrict__ nodes, long long n_elem, i
       lo[a] = fmin(lo[a], v);
       hi[a] = fmax(hi[a], v);
     }
+  double o[3];
   for (int a = 0; a < 3; ++a) {
-    box[6 * e + a] = __double2float_rd(lo[a]);
-    box[6 * e + 3 + a] = __double2float_ru(hi[a]);
+    const float bl = __double2float_rd(lo[a]), bh = __double2float_ru(hi[a]);
+    box[6 * e + a] = bl;
+    box[6 * e + 3 + a] = bh;
+    o[a] = 0.5 * ((double)bl + (double)bh);
   }
   if (nonfinite) atomicOr(bad, 1);
+  if (!loc) return;
+  for (int a = 0; a < 3; ++a) org[3 * e + a] = o[a];
+  for (int k = 0; k < npe; ++k)
+    for (int a = 0; a < 3; ++a) loc[e * 3 * npe + a * npe + k] = (float)(x[3 * k + a] - o[a]);
 }
 
 // ------------------------------------------------------------------ triangle tables
@@ -115,6 +125,8 @@ struct Mesh {
   long long n_elem = 0;
   double* nodes = nullptr;
   float* box = nullptr;
+  float* loc = nullptr;    // element-frame node coordinates [n_elem][3][npe]
+  double* org = nullptr;   // element frame origins [n_elem][3]
 };
 
 struct Arena {
@@ -133,10 +145,20 @@ struct LaunchParams {
   Inst* d_inst = nullptr;
   long long* d_off = nullptr;
   unsigned long long *cand = nullptr, *redo = nullptr, *d_cnt = nullptr;
+  // flags-only split of the exact stage (k_near1..3), when some instance
+  // asks for flags only
+  bool near = false;
+  unsigned* status = nullptr;
+  unsigned long long *task = nullptr, *full = nullptr, *pair = nullptr, *f64 = nullptr;
+  unsigned long long task_cap = 0, pair_cap = 0, f64_cap = 0;
+  float* tface = nullptr;
+  int tstride = 0;
   bool operator==(const LaunchParams& o) const {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
-           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt;
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && status == o.status &&
+           task == o.task && full == o.full && task_cap == o.task_cap && pair == o.pair && pair_cap == o.pair_cap &&
+           tface == o.tface && tstride == o.tstride && f64 == o.f64 && f64_cap == o.f64_cap;
   }
 };
 
@@ -180,10 +202,14 @@ struct Slot {
   long long out_n = 0;
   bool host_out = false;
   bool want_dist = false;
+  bool near = false;       // the flags-only split ran
   int cur_ring = 0;
 };
 
-constexpr int NCNT = 16;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters
+constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters,
+                          // [11] near tasks, [12] holes decided by the hole map,
+                          // [13] near pairs, [14,15] full-search list/cursor,
+                          // [16] near pairs given the full FP32 test, [17] near FP64 list
 
 }  // namespace
 
@@ -211,6 +237,13 @@ struct InstReq {
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// the smallest float >= x (x finite, positive)
+float float_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
 int nbins_cap(int bin_cubes) {
   int b = (MAX_DIM + bin_cubes - 1) / bin_cubes;
   return b * b * b;
@@ -235,6 +268,12 @@ void launch_components(Inst* d_inst, int n, cudaStream_t st) {
   k_run_states<<<g, 256, 0, st>>>(d_inst);
 }
 
+// (element, face) task capacity of the flags-only split; elements that find
+// it full fall back to the full search
+unsigned long long near_task_cap(long long ne_total) { return (unsigned long long)ne_total + 65536ull; }
+unsigned long long near_pair_cap(long long ne_total) { return 8ull * (unsigned long long)ne_total + 262144ull; }
+unsigned long long near_f64_cap(long long ne_total) { return (unsigned long long)ne_total / 8ull + 65536ull; }
+
 // bytes of arena a batch needs
 size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
   size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
@@ -248,6 +287,13 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
          run_bytes();
   }
   s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
+  int qmax = 1;
+  for (auto& r : v) qmax = std::max(qmax, (int)r.req->q);
+  s += al256(sizeof(unsigned) * ne_total) + al256(sizeof(unsigned long long) * near_task_cap(ne_total)) +
+       al256(sizeof(float) * 3 * (qmax + 1) * (qmax + 1) * near_task_cap(ne_total)) +
+       al256(sizeof(unsigned long long) * near_pair_cap(ne_total)) +
+       al256(sizeof(unsigned long long) * near_f64_cap(ne_total)) +
+       al256(sizeof(unsigned long long) * ne_total);  // near status, tasks, task faces, pairs, full-search list
   s += al256(sizeof(unsigned long long) * NCNT);
   s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
   return s;
@@ -371,7 +417,7 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
   if (prof) CK(record(s.ev[2], st, capturing));
   CandList cl{cand, (unsigned long long)ne_total, d_cnt};
   CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
-  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl);
+  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl, d_cnt + 12);
   if (prof) CK(record(s.ev[3], st, capturing));
   const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
   const int WPB = TB / 32;
@@ -382,7 +428,19 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
     occ = std::max(occ, 1);
-    k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
+    if (P.near) {
+      CandList fl{P.full, (unsigned long long)ne_total, d_cnt + 14};
+      NearBufs nb{P.status, P.task, P.task_cap, P.pair, P.pair_cap, P.tface, P.tstride, P.f64, P.f64_cap, d_cnt + 11};
+      k_near1<<<c->n_sm * 8, TB, 0, st>>>(d_inst, cl, fl, nb, d_cnt + 4);
+      k_near_pairs<<<c->n_sm * 6, TB, 0, st>>>(d_inst, cl, nb, d_cnt + 4);
+      k_near_cross<<<c->n_sm * 4, TB, 0, st>>>(d_inst, cl, nb);
+      k_near_eval<<<c->n_sm * 2, TB, 0, st>>>(d_inst, cl, nb, d_cnt + 4);
+      k_near_fp64<<<c->n_sm, TB, 0, st>>>(d_inst, cl, nb, d_cnt + 4);
+      k_near3<<<c->n_sm * 4, TB, 0, st>>>(d_inst, cl, fl, nb, d_cnt + 4);
+      k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, fl, rl, pmax, qmax, d_cnt + 4);
+    } else {
+      k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
+    }
     if (prof) CK(record(s.ev[5], st, capturing));
     // the FP64 redo pass is rarely non-empty: a small persistent grid keeps
     // its launch cheap
@@ -461,6 +519,8 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     int npf = (r->q + 1) * (r->q + 1);
     in.nodes = m.nodes;
     in.eaabb = m.box;
+    in.eloc = m.loc;
+    in.eorg = m.org;
     in.n_elem = m.n_elem;
     in.p = m.p;
     in.q = r->q;
@@ -496,6 +556,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
       in.zedge_cnt = (int*)take(sizeof(int) * MAX_DIM);
     }
     in.tol = c->cfg.tol;
+    in.tol_f = float_up(c->cfg.tol);
     in.holemap_cells = c->cfg.holemap_cells;
     in.bin_cubes = c->cfg.bin_cubes;
     in.want_dist = r->dist_out ? 1 : 0;
@@ -510,6 +571,13 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
+  unsigned* nstatus = (unsigned*)take(sizeof(unsigned) * ne_total);
+  unsigned long long* ntask = (unsigned long long*)take(sizeof(unsigned long long) * near_task_cap(ne_total));
+  unsigned long long* npair = (unsigned long long*)take(sizeof(unsigned long long) * near_pair_cap(ne_total));
+  const int tstride = 3 * (qmax + 1) * (qmax + 1);
+  float* ntface = (float*)take(sizeof(float) * tstride * near_task_cap(ne_total));
+  unsigned long long* nf64 = (unsigned long long*)take(sizeof(unsigned long long) * near_f64_cap(ne_total));
+  unsigned long long* nfull = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   int8_t* oflags = (int8_t*)take(ne_total);
   double* odist = (double*)take(sizeof(double) * ne_total);
   // outputs: caller's device buffers, or staging for host buffers
@@ -537,6 +605,15 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   lp.pmax = pmax; lp.qmax = qmax; lp.precision = c->cfg.precision; lp.prof = c->cfg.profile != 0;
   lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt;
   {
+    bool flags_only = false;
+    for (auto& r : v) flags_only |= r.req->dist_out == nullptr;
+    lp.near = c->cfg.precision == DC_FP32_RECHECK && flags_only && ne_total < (1LL << 31);
+    lp.status = nstatus; lp.task = ntask; lp.full = nfull; lp.task_cap = near_task_cap(ne_total);
+    lp.pair = npair; lp.pair_cap = near_pair_cap(ne_total);
+    lp.tface = ntface; lp.tstride = tstride;
+    lp.f64 = nf64; lp.f64_cap = near_f64_cap(ne_total);
+  }
+  {
     const ExLayout Ld = ex_layout(pmax, qmax, 8);
     if ((long long)Ld.total * (256 / 32) > c->smem_optin)
       return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * 8);
@@ -547,6 +624,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   s.n_inst = n;
   s.d_inst = d_inst;
   s.d_cnt = d_cnt;
+  s.near = lp.near;
   return DC_OK;
 }
 
@@ -571,7 +649,12 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
   S.pairs_bulk = (int64_t)s.h_cnt[5];
   S.pairs_recheck = (int64_t)s.h_cnt[6];
   S.n_fringe = (int64_t)s.h_cnt[7];
+  S.n_hole = (int64_t)(s.h_cnt[8] + s.h_cnt[12]);
+  S.n_field = S.n_elem - S.n_candidates - (int64_t)s.h_cnt[12] + (int64_t)s.h_cnt[9];
   S.fallbacks = (int64_t)s.h_cnt[10];
+  S.near_tasks = s.near ? (int64_t)s.h_cnt[11] : 0;
+  S.n_full_search = s.near ? (int64_t)s.h_cnt[14] : (int64_t)s.h_cnt[0];
+  S.near_pairs_full = s.near ? (int64_t)s.h_cnt[16] : 0;
   if (c->cfg.profile) {
     cudaEventElapsedTime(&S.ms_surface, s.ev[0], s.ev[1]);
     cudaEventElapsedTime(&S.ms_holemap, s.ev[1], s.ev[2]);
@@ -722,23 +805,26 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     c->pmax = std::max(c->pmax, md.p);
     size_t npe = (size_t)(md.p + 1) * (md.p + 1) * (md.p + 1);
     size_t nb = sizeof(double) * npe * 3 * md.n_elem, bb = sizeof(float) * 6 * md.n_elem;
-    if (cfg.mem_budget_bytes && c->mesh_bytes + nb + bb > cfg.mem_budget_bytes) {
+    size_t lb = sizeof(float) * npe * 3 * md.n_elem, ob = sizeof(double) * 3 * md.n_elem;
+    if (cfg.mem_budget_bytes && c->mesh_bytes + nb + bb + lb + ob > cfg.mem_budget_bytes) {
       cudaFree(d_bad);
       return bail(fail(DC_ENOMEM, "mesh %d does not fit the memory budget", i));
     }
-    if (cudaMalloc(&m.nodes, nb) != cudaSuccess || cudaMalloc(&m.box, bb) != cudaSuccess) {
+    if (cudaMalloc(&m.nodes, nb) != cudaSuccess || cudaMalloc(&m.box, bb) != cudaSuccess ||
+        cudaMalloc(&m.loc, lb) != cudaSuccess || cudaMalloc(&m.org, ob) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(d_bad);
-      return bail(fail(DC_ENOMEM, "mesh %d: cudaMalloc of %zu bytes failed", i, nb + bb));
+      return bail(fail(DC_ENOMEM, "mesh %d: cudaMalloc of %zu bytes failed", i, nb + bb + lb + ob));
     }
-    c->mesh_bytes += nb + bb;
+    c->mesh_bytes += nb + bb + lb + ob;
     cudaMemcpyKind kind = md.nodes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (cudaMemcpyAsync(m.nodes, md.nodes, nb, kind, st) != cudaSuccess) {
       cudaFree(d_bad);
       return bail(fail(DC_ECUDA, "mesh %d: copying nodes failed", i));
     }
     cudaMemsetAsync(d_bad, 0, sizeof(int), st);
-    k_elem_box<<<(unsigned)((md.n_elem + 255) / 256), 256, 0, st>>>(m.nodes, md.n_elem, (int)npe, m.box, d_bad);
+    k_elem_box<<<(unsigned)((md.n_elem + 255) / 256), 256, 0, st>>>(m.nodes, md.n_elem, (int)npe, m.box, m.loc, m.org,
+                                                                      d_bad);
     int bad = 0;
     if (cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -882,6 +968,8 @@ void dc_destroy(dc_ctx* c) {
   for (auto& m : c->meshes) {
     if (m.nodes) cudaFree(m.nodes);
     if (m.box) cudaFree(m.box);
+    if (m.loc) cudaFree(m.loc);
+    if (m.org) cudaFree(m.org);
   }
   delete c;
 }
@@ -1014,6 +1102,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   int* d_bad = (int*)take(sizeof(int));
   h.nbins_cap = nb;
   h.tol = tol;
+  h.tol_f = float_up(tol);
   h.holemap_cells = cells;
   h.bin_cubes = bin_cubes;
   h.want_dist = dist_out ? 1 : 0;
@@ -1025,7 +1114,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
   CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
   const int TB = 256;
-  k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, d_bad);
+  k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, nullptr, nullptr, d_bad);
   unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
   k_surface<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
   k_grid<<<1, 64, 0, st>>>(d_inst, 1);
@@ -1039,7 +1128,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CandList cl{cand, (unsigned long long)n_elem, d_cnt};
   CandList rl{redo, (unsigned long long)n_elem, d_cnt + 2};
   CandList none{redo, 0, d_cnt + 2};
-  k_classify<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(d_inst, d_off + 2, 1, n_elem, cl);
+  k_classify<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(d_inst, d_off + 2, 1, n_elem, cl, d_cnt + 12);
   const ExLayout Lf = ex_layout(p, q, 4), Ld = ex_layout(p, q, 8);
   const int WPB = TB / 32;
   if ((long long)Ld.total * WPB > D.smem_optin)

@@ -46,6 +46,9 @@ struct Inst {
   // background grid (resident)
   const double* nodes;   // [n_elem][(p+1)^3][3]
   const float* eaabb;    // [n_elem][6] element node boxes, rounded outward
+  const float* eloc;     // [n_elem][3][(p+1)^3] node coordinates in the element frame
+                         // (x block, y block, z block), float; null in the allocation-free cut
+  const double* eorg;    // [n_elem][3] element frame origins (centre of the float box)
   long long n_elem;
   int p;
   // cut surface
@@ -76,9 +79,9 @@ struct Inst {
   unsigned* root_label;    // per compact root: final label [ROOT_CAP]
   int* zedge;              // per slice: (root id, slot of the joined root below) pairs [MAX_DIM][2*ZEDGE_CAP]
   int* zedge_cnt;          // per slice [MAX_DIM]
-  int nroots;              // unused (kept for the layout of older tools)
   // parameters
   double tol;
+  float tol_f;             // tol rounded up to float
   int holemap_cells;
   int bin_cubes;
   int want_dist;

@@ -86,14 +86,15 @@ __host__ __device__ __forceinline__ bool in_tri(V3<T> X, V3<T> v0, V3<T> v1, V3<
 // triangle a) and cb (on b), 0 when an edge of one crosses the other; L: lower
 // bound, the gap between the projections of both triangles on (cb - ca).
 // xcode: -1, or which edge crossed: 0..2 edge j of b (b[j] -> b[j+1]) through
-// a, 3..5 edge j of a through b.
-template <class T>
+// a, 3..5 edge j of a through b.  UNROLL unrolls the vertex loops (vertices in
+// registers, for kernels with registers to spare); the arithmetic is the same.
+template <class T, bool UNROLL = false>
 __host__ __device__ void tritri(const V3<T> a[3], const V3<T> b[3], T& U, T& L, V3<T>& ca, V3<T>& cb, int& xcode) {
   xcode = -1;
   V3<T> na = cross(a[1] - a[0], a[2] - a[0]);
   V3<T> nb = cross(b[1] - b[0], b[2] - b[0]);
   T sb[3], sa[3];
-#pragma unroll 1
+#pragma unroll (UNROLL ? 3 : 1)
   for (int j = 0; j < 3; ++j) { sb[j] = dot(na, b[j] - a[0]); sa[j] = dot(nb, a[j] - b[0]); }
   bool sepB = (sb[0] > T(0) && sb[1] > T(0) && sb[2] > T(0)) || (sb[0] < T(0) && sb[1] < T(0) && sb[2] < T(0));
   bool sepA = (sa[0] > T(0) && sa[1] > T(0) && sa[2] > T(0)) || (sa[0] < T(0) && sa[1] < T(0) && sa[2] < T(0));
@@ -117,7 +118,7 @@ __host__ __device__ void tritri(const V3<T> a[3], const V3<T> b[3], T& U, T& L, 
   T na2 = dot(na, na), nb2 = dot(nb, nb);
   // vertex of one triangle over the interior of the other
   if (na2 > T(0)) {
-#pragma unroll 1
+#pragma unroll (UNROLL ? 3 : 1)
     for (int j = 0; j < 3; ++j) {
       V3<T> X = b[j] - (sb[j] / na2) * na;
       if (in_tri(X, a[0], a[1], a[2], na)) {
@@ -128,7 +129,7 @@ __host__ __device__ void tritri(const V3<T> a[3], const V3<T> b[3], T& U, T& L, 
     }
   }
   if (nb2 > T(0)) {
-#pragma unroll 1
+#pragma unroll (UNROLL ? 3 : 1)
     for (int j = 0; j < 3; ++j) {
       V3<T> X = a[j] - (sa[j] / nb2) * nb;
       if (in_tri(X, b[0], b[1], b[2], nb)) {
@@ -139,10 +140,10 @@ __host__ __device__ void tritri(const V3<T> a[3], const V3<T> b[3], T& U, T& L, 
     }
   }
   // edge pairs
-#pragma unroll 1
+#pragma unroll (UNROLL ? 3 : 1)
   for (int i = 0; i < 3; ++i) {
     V3<T> d1 = a[(i + 1) % 3] - a[i];
-#pragma unroll 1
+#pragma unroll (UNROLL ? 3 : 1)
     for (int j = 0; j < 3; ++j) {
       V3<T> cp, cq;
       T d2 = seg_seg2(a[i], d1, b[j], b[(j + 1) % 3] - b[j], cp, cq);

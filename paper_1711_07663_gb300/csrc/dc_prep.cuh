@@ -150,6 +150,13 @@ __device__ __forceinline__ int cube_floor(double x, int n) {
   return (int)floor(x);
 }
 
+// the same for float arguments
+__device__ __forceinline__ int cube_floorf(float x, int n) {
+  if (!(x > -1.0f)) return -1;
+  if (!(x < (float)n)) return n;
+  return (int)floorf(x);
+}
+
 // a3: NEAR tags of the hole map, and face -> bin (bin of the box's min corner)
 __global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total) {
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -648,11 +655,12 @@ struct CandList {
 };
 
 __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const long long* __restrict__ eoff, int n_inst,
-                                                  long long ne_total, CandList cl) {
+                                                  long long ne_total, CandList cl,
+                                                  unsigned long long* __restrict__ n_hole_map) {
   const unsigned FULL = 0xffffffffu;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = g < ne_total;
-  bool cand = false;
+  bool cand = false, hole = false;
   int ii = 0;
   long long e = 0;
   if (valid) {
@@ -707,10 +715,13 @@ __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const lo
       }
     }
     if (!cand) {
+      hole = flag == DC_HOLE_;
       in.flags[e] = flag;
       if (in.dist) in.dist[e] = (flag == DC_HOLE_) ? -HUGE_VAL : HUGE_VAL;
     }
   }
+  const unsigned hm = __ballot_sync(FULL, hole);
+  if (hm && (threadIdx.x & 31) == 0) atomicAdd(n_hole_map, (unsigned long long)__popc(hm));
   unsigned m = __ballot_sync(FULL, cand);
   if (m) {
     int lane = threadIdx.x & 31;

@@ -109,7 +109,8 @@ def test_invalid_arguments_are_status_codes():
 
 def test_memory_budget_admission():
     c = W.sphere_in_box(n=8, p=2, m=4, q=2, seed=3)
-    mesh_bytes = c.nodes.nbytes + c.n_elem * 24
+    # nodes, float boxes, float element-frame nodes, frame origins
+    mesh_bytes = c.nodes.nbytes + c.n_elem * 24 + c.nodes.nbytes // 2 + c.n_elem * 24
     with pytest.raises(dc.DirectCutError) as ei:
         dc.Context([(c.p, c.nodes)], mem_budget_bytes=mesh_bytes // 2)
     assert ei.value.status == dc.DC_ENOMEM
@@ -138,3 +139,23 @@ def test_graph_replay_equals_direct_launches(monkeypatch):
     for (f1, d1), (f2, d2) in zip(outs["graphs"], outs["direct"]):
         assert np.array_equal(f1, f2) and np.array_equal(d1, d2)
     assert np.array_equal(outs["graphs"][0][0], outs["graphs"][2][0])
+
+
+def test_stats_count_the_flags():
+    """n_fringe + n_hole + n_field cover every element and equal the flag
+    counts, with and without distances (the flags-only split and the full
+    search)."""
+    c = W.sphere_in_box(n=14, p=2, m=6, q=2, seed=23)
+    with dc.Context([(c.p, c.nodes)]) as ctx:
+        for want_dist in (False, True):
+            f = np.empty(c.n_elem, dtype=np.int8)
+            d = np.empty(c.n_elem) if want_dist else None
+            ctx.cut(0, c.q, c.faces, f, d)
+            st = ctx.stats()
+            assert st["n_elem"] == c.n_elem
+            assert st["n_fringe"] == int((f == dc.DC_FRINGE).sum())
+            assert st["n_hole"] == int((f == dc.DC_HOLE).sum())
+            assert st["n_field"] == int((f == dc.DC_FIELD).sum())
+            assert 0 <= st["n_full_search"] <= st["n_candidates"]
+            if want_dist:
+                assert st["near_tasks"] == 0 and st["n_full_search"] == st["n_candidates"]

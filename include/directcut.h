@@ -116,7 +116,8 @@ typedef struct {
     int64_t pairs_bulk;       /* triangle pairs evaluated in the bulk precision */
     int64_t pairs_recheck;    /* triangle pairs re-solved in FP64 */
     int64_t fallbacks;        /* elements redone in FP64 after a list overflow */
-    int64_t holemap_components; /* enclosed components found by the hole map */
+    int64_t holemap_rows_undecided; /* hole-map rows whose surface crossings could not be
+                                       certified (their cubes are left "near") */
     float ms_surface;         /* profile=1 only: pose + face boxes + hole map tags + bins */
     float ms_holemap;         /* connected components + winding-number seeds */
     float ms_classify;        /* hole-map lookup + candidate compaction */
@@ -185,7 +186,7 @@ const char *dc_last_error(void);
  * process exits; the call makes no cudaMalloc/cudaFree (nor any other
  * allocating call).  Sizes whose scratch does not fit are rejected with
  * DC_EINVAL and a message giving the bytes needed (40 bytes per element, about
- * 300 bytes per Q2 face or 700 per Q4 face, plus 2.4 MiB: 65,536 elements with
+ * 250 bytes per Q2 face or 630 per Q4 face, plus 2.6 MiB: 65,536 elements with
  * 8,192 Q2 faces fit).  The hole map uses 64 cubes on the longest side and 4-cube
  * face bins, the bulk tests FP32 with FP64 re-solve (flags identical to
  * dc_cut).

@@ -65,7 +65,7 @@ class dc_request(ctypes.Structure):
 class dc_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_elem", "n_candidates", "n_fringe", "n_hole", "n_field",
                                              "faces_visited", "pairs_bulk", "pairs_recheck", "fallbacks",
-                                             "holemap_components")] + \
+                                             "holemap_rows_undecided")] + \
                [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_redo",
                                                   "ms_total")] + \
                [(n, ctypes.c_int64) for n in ("near_tasks", "n_full_search", "near_pairs_full")]

@@ -140,7 +140,7 @@ struct Arena {
 // device before each launch, so one graph serves every request of a shape.
 struct LaunchParams {
   int n = 0;
-  long long nf_total = 0, ne_total = 0, max_tri = 0;
+  long long nf_total = 0, ne_total = 0, max_tri = 0, max_f = 0;
   int pmax = 1, qmax = 1, precision = 0, prof = 0;
   Inst* d_inst = nullptr;
   long long* d_off = nullptr;
@@ -154,7 +154,8 @@ struct LaunchParams {
   float* tface = nullptr;
   int tstride = 0;
   bool operator==(const LaunchParams& o) const {
-    return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && pmax == o.pmax &&
+    return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
+           pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
            cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && status == o.status &&
            task == o.task && full == o.full && task_cap == o.task_cap && pair == o.pair && pair_cap == o.pair_cap &&
@@ -251,21 +252,16 @@ int nbins_cap(int bin_cubes) {
 
 size_t cube_bytes() { return (size_t)MAX_DIM * MAX_DIM * CUBE_PITCH; }
 
-// hole-map run tables of one instance: counts, extents, parents, flags
+// hole-map row tables of one instance: crossing counts and crossings
 size_t run_bytes() {
-  const size_t rows = (size_t)MAX_DIM * MAX_DIM, slots = rows * RUNS_PER_ROW;
-  return al256(sizeof(int) * rows) + al256(sizeof(unsigned short) * slots) + al256(sizeof(int) * slots) +
-         al256(sizeof(unsigned) * slots) + 3 * al256(sizeof(int) * ROOT_CAP) +
-         al256(sizeof(int) * MAX_DIM * 2 * ZEDGE_CAP) + al256(sizeof(int) * MAX_DIM);
+  const size_t rows = (size_t)MAX_DIM * MAX_DIM;
+  return al256(sizeof(int) * rows) + al256(sizeof(int) * rows * ROW_XCAP);
 }
 
-// the hole-map component kernels over every row of every instance
-void launch_components(Inst* d_inst, int n, cudaStream_t st) {
-  dim3 g((MAX_DIM * MAX_DIM + 255) / 256, n);
-  k_runs<<<g, 256, 0, st>>>(d_inst);
-  k_slice_cc<<<dim3(MAX_DIM, n), 256, 0, st>>>(d_inst);
-  k_join_cc<<<n, 1024, 0, st>>>(d_inst);
-  k_run_states<<<g, 256, 0, st>>>(d_inst);
+// inside/outside of the hole-map cubes: row crossings, then row labels
+void launch_rows(Inst* d_inst, int n, long long max_tri, cudaStream_t st) {
+  k_row_cross<<<dim3((unsigned)((max_tri + 255) / 256), n), 256, 0, st>>>(d_inst);
+  k_row_label<<<dim3((MAX_DIM * MAX_DIM + 7) / 8, n), 256, 0, st>>>(d_inst);
 }
 
 // (element, face) task capacity of the flags-only split; elements that find
@@ -282,7 +278,7 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
     long long F = r.req->n_faces;
     int npf = (r.req->q + 1) * (r.req->q + 1);
     if (!r.req->on_device) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
-    s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(double) * F * 6) + al256(sizeof(float) * F * 6) +
+    s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(float) * F * 6) +
          al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) +
          run_bytes();
   }
@@ -405,15 +401,13 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
 
   const int TB = 256;
   unsigned gf = (unsigned)((nf_total + TB - 1) / TB);
-  k_surface<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
-  k_grid<<<(n + 63) / 64, 64, 0, st>>>(d_inst, n);
+  k_surface<<<dim3((unsigned)((P.max_f + SURF_FPB - 1) / SURF_FPB), n), TB, 0, st>>>(d_inst);
   k_clear<<<dim3(64, n), TB, 0, st>>>(d_inst);
   k_tag<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
   k_bin_scan<<<n, 1024, 0, st>>>(d_inst);
   k_bin_fill<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
   if (prof) CK(record(s.ev[1], st, capturing));
-  launch_components(d_inst, n, st);
-  k_winding<<<dim3((unsigned)((max_tri + TB - 1) / TB), MAX_COMP, n), TB, 0, st>>>(d_inst);
+  launch_rows(d_inst, n, max_tri, st);
   if (prof) CK(record(s.ev[2], st, capturing));
   CandList cl{cand, (unsigned long long)ne_total, d_cnt};
   CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
@@ -490,10 +484,11 @@ dc_status launch_graph(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t s
 // Enqueue the whole cut of a batch on slot s (no host synchronisation).
 dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool staged_out) {
   const int n = (int)v.size();
-  long long nf_total = 0, ne_total = 0, max_tri = 0;
+  long long nf_total = 0, ne_total = 0, max_tri = 0, max_f = 0;
   int pmax = 1, qmax = 1;
   for (auto& r : v) {
     nf_total += r.req->n_faces;
+    max_f = std::max<long long>(max_f, r.req->n_faces);
     ne_total += c->meshes[r.mesh].n_elem;
     max_tri = std::max<long long>(max_tri, r.req->n_faces * 2LL * r.req->q * r.req->q);
     pmax = std::max(pmax, c->meshes[r.mesh].p);
@@ -535,7 +530,6 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.has_pose = r->pose ? 1 : 0;
     if (r->pose) memcpy(in.pose, r->pose, sizeof(double) * 12);
     in.surf = (double*)take(sizeof(double) * F * npf * 3);
-    in.fbox64 = (double*)take(sizeof(double) * F * 6);
     in.fbox = (float*)take(sizeof(float) * F * 6);
     in.fbin = (int*)take(sizeof(int) * F);
     in.bin_faces = (int*)take(sizeof(int) * F);
@@ -544,16 +538,9 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.bin_off = (int*)take(sizeof(int) * (nb + 1));
     in.nbins_cap = nb;
     {
-      const size_t rows = (size_t)MAX_DIM * MAX_DIM, slots = rows * RUNS_PER_ROW;
-      in.run_cnt = (int*)take(sizeof(int) * rows);
-      in.run_xx = (unsigned short*)take(sizeof(unsigned short) * slots);
-      in.run_par = (int*)take(sizeof(int) * slots);
-      in.run_flag = (unsigned*)take(sizeof(unsigned) * slots);
-      in.root_info = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
-      in.root_slot = (int*)take(sizeof(int) * ROOT_CAP);
-      in.root_label = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
-      in.zedge = (int*)take(sizeof(int) * MAX_DIM * 2 * ZEDGE_CAP);
-      in.zedge_cnt = (int*)take(sizeof(int) * MAX_DIM);
+      const size_t rows = (size_t)MAX_DIM * MAX_DIM;
+      in.row_cnt = (int*)take(sizeof(int) * rows);
+      in.row_x = (int*)take(sizeof(int) * rows * ROW_XCAP);
     }
     in.tol = c->cfg.tol;
     in.tol_f = float_up(c->cfg.tol);
@@ -601,7 +588,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   CK(cudaEventRecord(s.ring_ev[s.cur_ring], st));
   s.ring_used[s.cur_ring] = true;
   LaunchParams lp;
-  lp.n = n; lp.nf_total = nf_total; lp.ne_total = ne_total; lp.max_tri = max_tri;
+  lp.n = n; lp.nf_total = nf_total; lp.ne_total = ne_total; lp.max_tri = max_tri; lp.max_f = max_f;
   lp.pmax = pmax; lp.qmax = qmax; lp.precision = c->cfg.precision; lp.prof = c->cfg.profile != 0;
   lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt;
   {
@@ -642,7 +629,7 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
   for (int i = 0; i < n; ++i) {
     err |= s.h_inst[i].err;
     S.n_elem += s.h_inst[i].n_elem;
-    S.holemap_components += s.h_inst[i].ncomp;
+    S.holemap_rows_undecided += s.h_inst[i].rows_undecided;
   }
   S.n_candidates = (int64_t)s.h_cnt[0];
   S.faces_visited = (int64_t)s.h_cnt[4];
@@ -1044,7 +1031,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   // scratch plan (bytes, 256-aligned pieces)
   size_t need = al256(sizeof(Inst)) + al256(sizeof(long long) * 4) + al256(sizeof(float) * 6 * n_elem) +
                 al256(sizeof(unsigned long long) * n_elem) * 2 + al256(sizeof(unsigned long long) * NCNT) +
-                al256(sizeof(double) * n_faces * npf * 3) + al256(sizeof(double) * n_faces * 6) +
+                al256(sizeof(double) * n_faces * npf * 3) +
                 al256(sizeof(float) * n_faces * 6) + al256(sizeof(int) * n_faces) * 2 + al256(cube_bytes()) +
                 al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) + run_bytes() + al256(sizeof(int));
   if (need > NOALLOC_SCRATCH_BYTES)
@@ -1080,7 +1067,6 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   h.flags = flags_out;
   h.dist = dist_out;
   h.surf = (double*)take(sizeof(double) * n_faces * npf * 3);
-  h.fbox64 = (double*)take(sizeof(double) * n_faces * 6);
   h.fbox = (float*)take(sizeof(float) * n_faces * 6);
   h.fbin = (int*)take(sizeof(int) * n_faces);
   h.bin_faces = (int*)take(sizeof(int) * n_faces);
@@ -1088,17 +1074,10 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   h.bin_cnt = (int*)take(sizeof(int) * nb);
   h.bin_off = (int*)take(sizeof(int) * (nb + 1));
   {
-      const size_t rows = (size_t)MAX_DIM * MAX_DIM, slots = rows * RUNS_PER_ROW;
-      h.run_cnt = (int*)take(sizeof(int) * rows);
-      h.run_xx = (unsigned short*)take(sizeof(unsigned short) * slots);
-      h.run_par = (int*)take(sizeof(int) * slots);
-      h.run_flag = (unsigned*)take(sizeof(unsigned) * slots);
-      h.root_info = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
-      h.root_slot = (int*)take(sizeof(int) * ROOT_CAP);
-      h.root_label = (unsigned*)take(sizeof(unsigned) * ROOT_CAP);
-      h.zedge = (int*)take(sizeof(int) * MAX_DIM * 2 * ZEDGE_CAP);
-      h.zedge_cnt = (int*)take(sizeof(int) * MAX_DIM);
-    }
+    const size_t rows = (size_t)MAX_DIM * MAX_DIM;
+    h.row_cnt = (int*)take(sizeof(int) * rows);
+    h.row_x = (int*)take(sizeof(int) * rows * ROW_XCAP);
+  }
   int* d_bad = (int*)take(sizeof(int));
   h.nbins_cap = nb;
   h.tol = tol;
@@ -1116,15 +1095,12 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   const int TB = 256;
   k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, nullptr, nullptr, d_bad);
   unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
-  k_surface<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
-  k_grid<<<1, 64, 0, st>>>(d_inst, 1);
+  k_surface<<<dim3((unsigned)((n_faces + SURF_FPB - 1) / SURF_FPB), 1), TB, 0, st>>>(d_inst);
   k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);
   k_tag<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
   k_bin_scan<<<1, 1024, 0, st>>>(d_inst);
   k_bin_fill<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
-  launch_components(d_inst, 1, st);
-  long long ntri = n_faces * 2LL * q * q;
-  k_winding<<<dim3((unsigned)((ntri + TB - 1) / TB), MAX_COMP, 1), TB, 0, st>>>(d_inst);
+  launch_rows(d_inst, 1, n_faces * 2LL * q * q, st);
   CandList cl{cand, (unsigned long long)n_elem, d_cnt};
   CandList rl{redo, (unsigned long long)n_elem, d_cnt + 2};
   CandList none{redo, 0, d_cnt + 2};

@@ -17,17 +17,14 @@ constexpr int MAX_NPF = (MAX_Q + 1) * (MAX_Q + 1);                // nodes per c
 constexpr int MAX_NTF = 2 * MAX_Q * MAX_Q;                        // triangles per cut face
 constexpr int MAX_CELLS = 80;                                     // hole-map cubes, longest side
 constexpr int MAX_DIM = MAX_CELLS + 2;                            // + one padding cube per side
-constexpr int MAX_COMP = 4;   // enclosed hole-map components resolved by a winding number
-constexpr int RUNS_PER_ROW = 24;  // run slots per hole-map row (a row with more is made NEAR)
-constexpr int ROOTS_PER_SLICE = 48;                       // slice components (more: the map degrades to NEAR)
-constexpr int ROOT_CAP = ROOTS_PER_SLICE * (MAX_CELLS + 2); // compact root ids, ROOTS_PER_SLICE per slice
-constexpr int ZEDGE_CAP = 512;    // distinct (root, lower run) joins between a slice and the one below
+constexpr int ROW_XCAP = 24;  // surface crossings recorded per hole-map row (a row with more stays NEAR)
 
 // hole-map cube states (Sec. 4.2 hole maps, after the 0/1 flip):
-//   OUT  = reached from the border, outside the surface
-//   NEAR = overlapped by a face box inflated by the fringe margin ("2")
-//   COMP0 + k = k-th enclosed component; inside iff its winding number is 1
-constexpr uint8_t CUBE_OUT = 0, CUBE_NEAR = 2, CUBE_COMP0 = 3;
+//   OUT  = outside the surface (winding number 0)
+//   IN   = inside the surface (winding number 1)
+//   NEAR = overlapped by a face box inflated by the fringe margin ("2"), or
+//          on a row whose crossings could not be certified
+constexpr uint8_t CUBE_OUT = 0, CUBE_IN = 1, CUBE_NEAR = 2;
 
 // flag values written to the per-element int8 output
 constexpr int8_t DC_HOLE_ = 0, DC_FIELD_ = 1, DC_FRINGE_ = -1;
@@ -35,8 +32,6 @@ constexpr int8_t DC_HOLE_ = 0, DC_FIELD_ = 1, DC_FRINGE_ = -1;
 // error bits reported per instance
 enum : int {
   ERR_ROUNDS = 1,        // face gather did not converge
-  ERR_RUNS = 2,          // hole-map run table overflow (map degraded to "near")
-  ERR_WINDING = 4,       // winding number of a component not near 0 or 1
   ERR_RECHECK = 8,       // FP64 tie list overflow in the FP64 path
   ERR_DEGENERATE = 16,   // zero-extent surface
   ERR_NONFINITE = 64,    // a face node is NaN or infinite
@@ -62,23 +57,15 @@ struct Inst {
   double* dist;            // may be null
   // scratch (per instance)
   double* surf;            // posed face nodes [n_faces][(q+1)^2][3]
-  double* fbox64;          // face node boxes [n_faces][6]
-  float* fbox;             // same, float, rounded outward
+  float* fbox;             // face node boxes [n_faces][6], float, rounded outward
   int* fbin;               // bin of each face
   uint8_t* cube;           // hole map [dims z][y][x]
   int* bin_cnt;            // [nbins]
   int* bin_off;            // [nbins + 1]
   int* bin_faces;          // [n_faces]
   int nbins_cap;
-  int* run_cnt;            // hole-map runs per row [rows]
-  unsigned short* run_xx;  // run extents x0 | x1 << 8 [rows][RUNS_PER_ROW]
-  int* run_par;            // union-find parents [rows][RUNS_PER_ROW]
-  unsigned* run_flag;      // compact id of each slice-root slot [rows][RUNS_PER_ROW]
-  unsigned* root_info;     // per compact root: border bit [ROOT_CAP]
-  int* root_slot;          // per compact root: its slot [ROOT_CAP]
-  unsigned* root_label;    // per compact root: final label [ROOT_CAP]
-  int* zedge;              // per slice: (root id, slot of the joined root below) pairs [MAX_DIM][2*ZEDGE_CAP]
-  int* zedge_cnt;          // per slice [MAX_DIM]
+  int* row_cnt;            // surface crossings per hole-map row [rows] (+ROW_UNDECIDED: undecided)
+  int* row_x;              // crossings (cube x << 1 | entering) [rows][ROW_XCAP]
   // parameters
   double tol;
   float tol_f;             // tol rounded up to float
@@ -88,6 +75,7 @@ struct Inst {
   // derived on the device
   unsigned long long sbox_key[6];  // order-preserving keys of the surface box
   unsigned int fext_bits[3];       // largest face-box extent per axis (float bits)
+  unsigned int surf_done;          // blocks of k_surface finished
   double origin[3];
   double ds;
   int dims[3];
@@ -95,9 +83,7 @@ struct Inst {
   int bdims[3];
   float origin_f[3];               // float copies for the bulk lookups (margins cover
   float inv_ds_f, inv_bs_f;        // their rounding)
-  int ncomp;
-  int comp_seed[MAX_COMP];
-  float comp_w[MAX_COMP];
+  int rows_undecided;              // hole-map rows left NEAR
   int err;
   // counters
   unsigned long long n_cand, n_fringe, n_hole, n_field;

@@ -648,8 +648,8 @@ __device__ __noinline__ int side_of(const Inst& in, int q, const double* o, cons
 }
 
 // hole-map label of a point: 1 inside, 2 outside, 0 undecided (near a cube
-// face, in a NEAR cube, or in an enclosed component whose winding number is
-// not near 0 or 1).  Float arithmetic; `m` (in cube units) covers its rounding.
+// face, or in a NEAR cube).  Float arithmetic; `m` (in cube units) covers its
+// rounding.
 __device__ __forceinline__ int point_label(const Inst& in, float x, float y, float z, float m) {
   float c[3] = {(x - in.origin_f[0]) * in.inv_ds_f, (y - in.origin_f[1]) * in.inv_ds_f,
                 (z - in.origin_f[2]) * in.inv_ds_f};
@@ -663,11 +663,7 @@ __device__ __forceinline__ int point_label(const Inst& in, float x, float y, flo
   }
   uint8_t s = in.cube[((long long)ix[2] * in.dims[1] + ix[1]) * CUBE_PITCH + ix[0]];
   if (s == CUBE_OUT) return 2;
-  if (s >= CUBE_COMP0 && s < CUBE_COMP0 + MAX_COMP) {
-    float w = in.comp_w[s - CUBE_COMP0];
-    if (w > 0.75f && w < 1.25f) return 1;
-    if (w > -0.25f && w < 0.25f) return 2;
-  }
+  if (s == CUBE_IN) return 1;
   return 0;
 }
 

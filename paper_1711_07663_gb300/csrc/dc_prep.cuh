@@ -27,91 +27,22 @@ __constant__ unsigned char c_ftri[MAX_Q][MAX_NTF][3];   // cut-face triangles, p
 constexpr int CUBE_PITCH = 96;  // bytes per x-row of the hole map (>= MAX_DIM, 16-byte multiple)
 
 // ------------------------------------------------------------------ a1 + a2
-// Pose transform (rounded exactly as ((R0 x + R1 y) + R2 z) + t, no fusion),
-// per-face node boxes, surface box and largest face extent.
-__global__ void k_surface(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst,
-                          long long nf_total) {
-  const unsigned FULL = 0xffffffffu;
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  bool valid = g < nf_total;
-  int ii = valid ? find_inst(foff, n_inst, g) : 0;
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  bool bad = false;
-  if (valid) {
-    Inst& in = I[ii];
-    long long f = g - foff[ii];
-    int npf = (in.q + 1) * (in.q + 1);
-    const double* src = in.faces_in + f * npf * 3;
-    double* dst = in.surf + f * npf * 3;
-    for (int k = 0; k < npf; ++k) {
-      double x = src[3 * k], y = src[3 * k + 1], z = src[3 * k + 2];
-      double o[3];
-      if (in.has_pose) {
-        for (int a = 0; a < 3; ++a) {
-          const double* R = in.pose + 4 * a;
-          o[a] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[0], x), __dmul_rn(R[1], y)), __dmul_rn(R[2], z)), R[3]);
-        }
-      } else {
-        o[0] = x; o[1] = y; o[2] = z;
-      }
-      for (int a = 0; a < 3; ++a) {
-        dst[3 * k + a] = o[a];
-        bad |= !(fabs(o[a]) < 1e300);
-        lo[a] = fmin(lo[a], o[a]);
-        hi[a] = fmax(hi[a], o[a]);
-      }
-    }
-    for (int a = 0; a < 3; ++a) {
-      in.fbox64[6 * f + a] = lo[a];
-      in.fbox64[6 * f + 3 + a] = hi[a];
-      in.fbox[6 * f + a] = __double2float_rd(lo[a]);
-      in.fbox[6 * f + 3 + a] = __double2float_ru(hi[a]);
-      atomicMax(&in.fext_bits[a], __float_as_uint(__double2float_ru(hi[a] - lo[a]) * 1.000001f));
-    }
-    if (bad) atomicOr(&in.err, (int)ERR_NONFINITE);
-  }
-  int i0 = __shfl_sync(FULL, ii, 0);
-  bool same = __all_sync(FULL, !valid || ii == i0);
-  if (same) {
-    for (int a = 0; a < 3; ++a) {
-      for (int s = 16; s; s >>= 1) {
-        lo[a] = fmin(lo[a], __shfl_xor_sync(FULL, lo[a], s));
-        hi[a] = fmax(hi[a], __shfl_xor_sync(FULL, hi[a], s));
-      }
-    }
-    if ((threadIdx.x & 31) == 0 && lo[0] <= hi[0]) {
-      Inst& in = I[i0];
-      for (int a = 0; a < 3; ++a) {
-        atomicMin(&in.sbox_key[a], dkey(lo[a]));
-        atomicMax(&in.sbox_key[3 + a], dkey(hi[a]));
-      }
-    }
-  } else if (valid) {
-    Inst& in = I[ii];
-    for (int a = 0; a < 3; ++a) {
-      atomicMin(&in.sbox_key[a], dkey(lo[a]));
-      atomicMax(&in.sbox_key[3 + a], dkey(hi[a]));
-    }
-  }
-}
+constexpr int SURF_FPB = 32;  // faces per block of k_surface
 
-// hole-map and bin geometry from the surface box (one thread per instance)
-__global__ void k_grid(Inst* __restrict__ I, int n_inst) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_inst) return;
-  Inst& in = I[i];
+// hole-map and bin geometry of one instance from its surface box
+__device__ void grid_from_box(Inst& in) {
   double lo[3], hi[3], L = 0.0;
   for (int a = 0; a < 3; ++a) {
-    lo[a] = dkey_decode(in.sbox_key[a]);
-    hi[a] = dkey_decode(in.sbox_key[3 + a]);
+    lo[a] = dkey_decode(atomicOr(&in.sbox_key[a], 0ull));
+    hi[a] = dkey_decode(atomicOr(&in.sbox_key[3 + a], 0ull));
     L = fmax(L, hi[a] - lo[a]);
   }
   if (!(L > 0.0) || !(L < 1e300)) {
-    in.err |= ERR_DEGENERATE;
+    atomicOr(&in.err, (int)ERR_DEGENERATE);
     L = 1.0;
   }
-  int cells = in.holemap_cells;
-  double ds = L / cells;
+  const int cells = in.holemap_cells;
+  const double ds = L / cells;
   in.ds = ds;
   int nb = 1;
   for (int a = 0; a < 3; ++a) {
@@ -127,7 +58,86 @@ __global__ void k_grid(Inst* __restrict__ I, int n_inst) {
   for (int a = 0; a < 3; ++a) in.origin_f[a] = (float)in.origin[a];
   in.inv_ds_f = (float)(1.0 / ds);
   in.inv_bs_f = (float)(1.0 / in.bs);
-  if (nb > in.nbins_cap) in.err |= ERR_DEGENERATE;  // sized on the host for the worst case
+  if (nb > in.nbins_cap) atomicOr(&in.err, (int)ERR_DEGENERATE);  // sized on the host for the worst case
+}
+
+// Pose transform (rounded exactly as ((R0 x + R1 y) + R2 z) + t, no fusion),
+// per-face node boxes, surface box and largest face extent.  Grid (blocks of
+// SURF_FPB faces, instances): threads transform nodes, then one thread per
+// (face, axis) takes the face's box from shared memory; the last block of an
+// instance to finish derives its hole-map grid.
+__global__ void __launch_bounds__(256) k_surface(Inst* __restrict__ I) {
+  __shared__ double s_x[SURF_FPB * MAX_NPF * 3];
+  __shared__ unsigned long long s_key[6];
+  __shared__ unsigned s_ext[3];
+  __shared__ int s_last;
+  Inst& in = I[blockIdx.y];
+  const long long F = in.n_faces;
+  const long long f0 = (long long)blockIdx.x * SURF_FPB;
+  if (f0 >= F) return;
+  const int nf = (int)min((long long)SURF_FPB, F - f0);
+  const int npf = (in.q + 1) * (in.q + 1);
+  const int nval = nf * npf * 3;
+  if (threadIdx.x < 6) s_key[threadIdx.x] = threadIdx.x < 3 ? ~0ull : 0ull;
+  if (threadIdx.x < 3) s_ext[threadIdx.x] = 0u;
+  const double* src = in.faces_in + f0 * npf * 3;
+  double* dst = in.surf + f0 * npf * 3;
+  bool bad = false;
+  if (in.has_pose) {
+    for (int k = threadIdx.x; k < nf * npf; k += blockDim.x) {
+      const double x = src[3 * k], y = src[3 * k + 1], z = src[3 * k + 2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double* R = in.pose + 4 * a;
+        const double v = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[0], x), __dmul_rn(R[1], y)), __dmul_rn(R[2], z)), R[3]);
+        s_x[3 * k + a] = v;
+        dst[3 * k + a] = v;
+        bad |= !(fabs(v) < 1e300);
+      }
+    }
+  } else {
+    for (int k = threadIdx.x; k < nval; k += blockDim.x) {
+      const double v = src[k];
+      s_x[k] = v;
+      dst[k] = v;
+      bad |= !(fabs(v) < 1e300);
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&in.err, (int)ERR_NONFINITE);
+  // face boxes: thread (face, axis)
+  if (threadIdx.x < nf * 3) {
+    const int lf = threadIdx.x / 3, a = threadIdx.x - lf * 3;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = 0; k < npf; ++k) {
+      const double v = s_x[(lf * npf + k) * 3 + a];
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+    }
+    const long long f = f0 + lf;
+    in.fbox[6 * f + a] = __double2float_rd(lo);
+    in.fbox[6 * f + 3 + a] = __double2float_ru(hi);
+    atomicMin(&s_key[a], dkey(lo));
+    atomicMax(&s_key[3 + a], dkey(hi));
+    atomicMax(&s_ext[a], __float_as_uint(__double2float_ru(hi - lo) * 1.000001f));
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    atomicMin(&in.sbox_key[threadIdx.x], s_key[threadIdx.x]);
+    atomicMax(&in.sbox_key[3 + threadIdx.x], s_key[3 + threadIdx.x]);
+    atomicMax(&in.fext_bits[threadIdx.x], s_ext[threadIdx.x]);
+  }
+  // the last block of this instance derives the grid
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned nblk = (unsigned)((F + SURF_FPB - 1) / SURF_FPB);
+    s_last = atomicAdd(&in.surf_done, 1u) == nblk - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    grid_from_box(in);
+  }
 }
 
 __global__ void k_clear(Inst* __restrict__ I) {
@@ -141,6 +151,8 @@ __global__ void k_clear(Inst* __restrict__ I) {
     c4[k] = make_uint4(0, 0, 0, 0);
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += (long long)gridDim.x * blockDim.x)
     in.bin_cnt[k] = 0;
+  const int nrows = in.dims[1] * in.dims[2];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nrows; k += gridDim.x * blockDim.x) in.row_cnt[k] = 0;
 }
 
 __device__ __forceinline__ int cube_floor(double x, int n) {
@@ -229,422 +241,190 @@ __global__ void k_bin_fill(Inst* __restrict__ I, const long long* __restrict__ f
   in.bin_faces[pos] = (int)f;
 }
 
-// ------------------------------------------------------------------ a3: components
-// The non-NEAR cubes of each x-row form runs; runs of face-adjacent rows that
-// overlap in x are connected.  Five small kernels over all rows of all
-// instances: runs into fixed per-row slots, union-find in global memory
-// (hooks by atomicCAS at L2, larger root onto smaller, so parents always point
-// to smaller slots and finds terminate), flatten + mark the components that
-// touch the map border (outside), number the enclosed ones, write the states.
-constexpr unsigned RUN_OUT = 1u, RUN_UNKNOWN = 2u;  // run_flag bits; component id in bits 4..
+// ------------------------------------------------------------------ a3: inside / outside
+// Every cube that no inflated face box touches lies wholly on one side of the
+// closed surface.  Its side is read off the winding number at the centre line
+// of its x-row (y, z fixed at the row's cube centres): starting at 0 in the
+// padding cube, the winding number changes by -1 at each surface triangle the
+// line leaves the body through (normal x component > 0) and +1 at each it
+// enters through, and those crossings lie in NEAR cubes.  The paper fills the
+// non-NEAR cubes from the map's border instead; for a closed surface the two
+// agree wherever the fill reaches, and the winding number also settles
+// cavities the fill cannot reach.
+//
+// Whether the line at p = (y_c, z_c) meets triangle ABC is decided by the
+// exact signs of the edge functions E(U->V; p) = (V_y - U_y)(p_z - U_z) -
+// (V_z - U_z)(p_y - U_y) of the FP64 vertices: a float evaluation with an
+// error bound first, then an FP64 one with the static bound of Shewchuk's
+// orientation test, then the exact value as a floating-point expansion
+// (error-free sums and FMA products).  An exact zero is resolved by simulation
+// of simplicity, moving p to (p_y + e, p_z + e^2) for an infinitesimal e, so
+// that every crossing of the watertight triangulated surface is counted
+// exactly once.
 
-__device__ __forceinline__ void row_mask(const uint8_t* row, int nx, unsigned long long& m0, unsigned long long& m1) {
-  // bit x set when cube x of the row is not NEAR
-  const uint4* r4 = reinterpret_cast<const uint4*>(row);
-  m0 = 0ull;
-  m1 = 0ull;
-#pragma unroll
-  for (int w = 0; w < CUBE_PITCH / 16; ++w) {
-    uint4 v = r4[w];
-    unsigned wd[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int by = 0; by < 4; ++by) {
-        int x = w * 16 + j * 4 + by;
-        unsigned char c = (wd[j] >> (8 * by)) & 0xffu;
-        if (x < nx && c != CUBE_NEAR) {
-          if (x < 64) m0 |= 1ull << x; else m1 |= 1ull << (x - 64);
-        }
-      }
-  }
+// Knuth's two-sum and the FMA two-product: s + e equals the exact result
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bv = __dsub_rn(s, a), av = __dsub_rn(s, bv);
+  e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
+  p = __dmul_rn(a, b);
+  e = __fma_rn(a, b, -p);
 }
 
-// first set bit at or after x of the 128-bit mask (m0 low word), or 128
-__device__ __forceinline__ int next_set(unsigned long long m0, unsigned long long m1, int x) {
-  if (x < 64) {
-    unsigned long long t = m0 & (~0ull << x);
-    if (t) return __ffsll((long long)t) - 1;
-    return m1 ? 64 + __ffsll((long long)m1) - 1 : 128;
-  }
-  if (x >= 128) return 128;
-  unsigned long long t = m1 & (~0ull << (x - 64));
-  return t ? 64 + __ffsll((long long)t) - 1 : 128;
-}
-
-__device__ __forceinline__ int rows_of(const Inst& in) { return in.dims[1] * in.dims[2]; }
-
-// 1. runs of each row into slots (grid.y = instance)
-__global__ void k_runs(Inst* __restrict__ I) {
-  Inst& in = I[blockIdx.y];
-  if (in.err & ERR_DEGENERATE) return;
-  const int nx = in.dims[0], nrows = rows_of(in);
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
-    unsigned long long m0, m1;
-    uint8_t* row = in.cube + (long long)r * CUBE_PITCH;
-    row_mask(row, nx, m0, m1);
-    int n = 0, x = 0;
-    bool over = false;
-    while (true) {
-      int x0 = next_set(m0, m1, x);
-      if (x0 >= nx) break;
-      int x1 = min(next_set(~m0, ~m1, x0), nx) - 1;
-      if (n == RUNS_PER_ROW) { over = true; break; }
-      int sl = r * RUNS_PER_ROW + n;
-      in.run_xx[sl] = (unsigned short)(x0 | (x1 << 8));
-      ++n;
-      x = x1 + 1;
-    }
-    if (over) {
-      // too many runs: make the row NEAR (walls only split components, and
-      // every enclosed component is labelled by its winding number)
-      for (int k = 0; k < nx; ++k) row[k] = CUBE_NEAR;
-      n = 0;
-    }
-    in.run_cnt[r] = n;
-  }
-}
-
-__device__ __forceinline__ bool overlap(unsigned short a, unsigned short b) {
-  return (int)(a & 0xff) <= (int)(b >> 8) && (int)(b & 0xff) <= (int)(a >> 8);
-}
-
-// union-find over shared-memory parents that always point to smaller slots
-// (path halving; hooks by atomicCAS of the larger root onto the smaller)
-__device__ int uf_find(volatile int* parent, int i) {
-  int p = parent[i];
-  while (p != i) {
-    int gp = parent[p];
-    if (gp != p) parent[i] = gp;
-    i = p;
-    p = parent[i];
-  }
-  return i;
-}
-
-// root walk without writes: compression must first read every root this
-// way, then (after a barrier) store them, because a concurrent path-splitting
-// write could otherwise replace a stored root by an intermediate ancestor
-__device__ __forceinline__ int uf_root(const volatile int* parent, int i) {
-  int p;
-  while ((p = parent[i]) != i) i = p;
-  return i;
-}
-
-__device__ void uf_union(volatile int* parent, int a, int b) {
-  while (true) {
-    a = uf_find(parent, a);
-    b = uf_find(parent, b);
-    if (a == b) return;
-    if (a < b) { int t = a; a = b; b = t; }
-    if (atomicCAS((int*)&parent[a], a, b) == a) return;
-  }
-}
-
-// 2. components inside each z-slice, in shared memory (one CTA per slice and
-//    instance).  Runs of rows y and y-1 that overlap are joined; every run
-//    records its slice root (the smallest slot of its slice component) in
-//    run_par, every slice root gets a compact id (run_flag of the root slot),
-//    its border bit and slot.  Each distinct (root of slice z, run of slice
-//    z-1) overlap is emitted once; the join resolves the lower run's root.
-// Labels of the runs of one slice by log-depth merging: in round w, the row
-// blocks [2kw, 2kw+w) and [2kw+w, 2kw+2w) are joined across their boundary
-// rows (every boundary y >= 1 is joined in exactly one round, w = its lowest
-// set bit), one thread per boundary; then every run is relinked to its root
-// (read all roots, barrier, write), so the trees stay flat and no find walks
-// a chain.  One row per thread: ny <= blockDim.  Ends with parents = roots =
-// the smallest slot of each component.
-__device__ void slice_label(volatile int* par, const unsigned short* xx, const unsigned char* cnt, int ny) {
-  const int y = threadIdx.x;
-  const int n = y < ny ? cnt[y] : 0;
-  for (int w = 1; w < ny; w <<= 1) {
-    // boundary rows of this round: y = (2k+1) w
-    if (y < ny && y >= w && ((y / w) & 1) && (y % w) == 0) {
-      const int m = cnt[y - 1];
-      for (int k = 0; k < n; ++k)
-        for (int j = 0; j < m; ++j)
-          if (overlap(xx[y * RUNS_PER_ROW + k], xx[(y - 1) * RUNS_PER_ROW + j]))
-            uf_union(par, y * RUNS_PER_ROW + k, (y - 1) * RUNS_PER_ROW + j);
-    }
-    __syncthreads();
-    int rr[RUNS_PER_ROW];
-    for (int k = 0; k < n; ++k) rr[k] = uf_root(par, y * RUNS_PER_ROW + k);
-    __syncthreads();
-    for (int k = 0; k < n; ++k) par[y * RUNS_PER_ROW + k] = rr[k];
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(256) k_slice_cc(Inst* __restrict__ I) {
-  constexpr int SL = MAX_DIM * RUNS_PER_ROW;
-  __shared__ int par[SL];
-  __shared__ unsigned short xx[SL], xxd[SL];
-  __shared__ unsigned char cnt[MAX_DIM], cntd[MAX_DIM];
-  __shared__ unsigned bord[SL];
-  constexpr int HB = 2 * ZEDGE_CAP;                 // hash buckets for the distinct joins
-  __shared__ unsigned long long ekeys[HB];
-  __shared__ int s_ne, s_full, s_nloc;
-  Inst& in = I[blockIdx.y];
-  if (in.err & ERR_DEGENERATE) return;
-  const int nx = in.dims[0], ny = in.dims[1], nz = in.dims[2];
-  const int z = blockIdx.x;
-  if (z >= nz) return;
-  const int r0 = z * ny, rd0 = (z - 1) * ny;
-  if (threadIdx.x == 0) { s_ne = 0; s_full = 0; s_nloc = 0; }
-  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
-    cnt[y] = (unsigned char)in.run_cnt[r0 + y];
-    cntd[y] = z > 0 ? (unsigned char)in.run_cnt[rd0 + y] : 0;
-  }
-  // the set of joins starts empty: shared memory may still hold keys of an
-  // earlier block (the same slice of another instance has the same slots)
-  for (int t = threadIdx.x; t < HB; t += blockDim.x) ekeys[t] = ~0ull;
-  for (int k = threadIdx.x; k < ny * RUNS_PER_ROW; k += blockDim.x) {
-    par[k] = k;
-    bord[k] = 0u;
-    xx[k] = in.run_xx[r0 * RUNS_PER_ROW + k];
-    xxd[k] = z > 0 ? in.run_xx[rd0 * RUNS_PER_ROW + k] : 0;
-  }
-  __syncthreads();
-  static_assert(MAX_DIM <= 256, "one row per thread");
-  slice_label(par, xx, cnt, ny);
-  // border bits of the slice roots; root slots, ids
-  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
-    const int n = cnt[y];
-    for (int k = 0; k < n; ++k) {
-      const int sl = y * RUNS_PER_ROW + k;
-      unsigned short a = xx[sl];
-      bool b = y == 0 || y == ny - 1 || z == 0 || z == nz - 1 || (a & 0xff) == 0 || (int)(a >> 8) == nx - 1;
-      if (b && !(((volatile unsigned*)bord)[par[sl]] & 1u)) atomicOr(&bord[par[sl]], 1u);
-      in.run_par[(r0 + y) * RUNS_PER_ROW + k] = r0 * RUNS_PER_ROW + par[sl];
-    }
-  }
-  __syncthreads();
-  // compact ids of this slice's roots: the range [z R, z R + R), R = ROOTS_PER_SLICE
-  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
-    const int n = cnt[y];
-    for (int k = 0; k < n; ++k) {
-      const int sl = y * RUNS_PER_ROW + k;
-      if (par[sl] != sl) continue;
-      int loc = atomicAdd(&s_nloc, 1);
-      if (loc >= ROOTS_PER_SLICE) continue;
-      const int id = z * ROOTS_PER_SLICE + loc;
-      const int gs = r0 * RUNS_PER_ROW + sl;
-      in.run_flag[gs] = (unsigned)id;
-      in.root_info[id] = bord[sl];
-      in.root_slot[id] = gs;
-    }
-  }
-  __syncthreads();
-  for (int t = s_nloc + threadIdx.x; t < ROOTS_PER_SLICE; t += blockDim.x) in.root_slot[z * ROOTS_PER_SLICE + t] = -1;
-  // distinct joins with slice z-1: key = (root slot here, root slot below)
-  if (z > 0) {
-    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
-      const int n = cnt[y], m = cntd[y];
-      for (int k = 0; k < n; ++k) {
-        const int sl = y * RUNS_PER_ROW + k;
-        for (int j = 0; j < m; ++j) {
-          const int sd = y * RUNS_PER_ROW + j;
-          if (!overlap(xx[sl], xxd[sd])) continue;
-          unsigned long long key = ((unsigned long long)(r0 * RUNS_PER_ROW + par[sl]) << 32) |
-                                   (unsigned)(rd0 * RUNS_PER_ROW + sd);
-          // shared hash set, open addressing, bounded probing
-          unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (HB - 1);
-          bool done = false;
-          for (int probe = 0; probe < HB && !done; ++probe) {
-            unsigned long long old = atomicCAS(&ekeys[h], ~0ull, key);
-            done = (old == ~0ull || old == key);
-            h = (h + 1) & (HB - 1);
+// Exact sign of (Qy - Py)(pz - Pz) - (Qz - Pz)(py - Py) (products of exact
+// two-term differences, summed into a nonoverlapping expansion; exact unless
+// a product underflows), then the simulation-of-simplicity terms for a zero.
+__device__ __noinline__ int edge_sign_exact(const double* P, const double* Q, double py, double pz) {
+  double a[2], b[2], c[2], d[2];
+  two_sum(Q[1], -P[1], a[1], a[0]);
+  two_sum(pz, -P[2], b[1], b[0]);
+  two_sum(Q[2], -P[2], c[1], c[0]);
+  two_sum(py, -P[1], d[1], d[0]);
+  double h[17];
+  int m = 0;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k) {
+        double t[2];
+        if (k == 0) two_prod(a[i], b[j], t[0], t[1]);
+        else { two_prod(c[i], d[j], t[0], t[1]); t[0] = -t[0]; t[1] = -t[1]; }
+        for (int r = 0; r < 2; ++r) {
+          // grow the expansion h by t[r]
+          double qv = t[r];
+          int w = 0;
+          for (int u = 0; u < m; ++u) {
+            double sum, err;
+            two_sum(qv, h[u], sum, err);
+            if (err != 0.0) h[w++] = err;
+            qv = sum;
           }
-          if (!done) s_full = 1;
+          if (qv != 0.0 || w == 0) h[w++] = qv;
+          m = w;
         }
       }
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < HB; t += blockDim.x) {
-    unsigned long long k = ekeys[t];
-    if (k == ~0ull) continue;
-    int pos = atomicAdd(&s_ne, 1);
-    if (pos < ZEDGE_CAP) {
-      in.zedge[z * 2 * ZEDGE_CAP + 2 * pos] = (int)(k >> 32);
-      in.zedge[z * 2 * ZEDGE_CAP + 2 * pos + 1] = (int)(k & 0xffffffffu);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (s_nloc > ROOTS_PER_SLICE) atomicOr(&in.err, (int)ERR_RUNS);
-    if (s_full || s_ne > ZEDGE_CAP) {
-      atomicOr(&in.err, (int)ERR_RUNS);  // the join degrades the map to NEAR: still exact
-      in.zedge_cnt[z] = 0;
-    } else {
-      in.zedge_cnt[z] = s_ne;
-    }
-  }
+  for (int u = m - 1; u >= 0; --u)
+    if (h[u] != 0.0) return h[u] > 0.0 ? 1 : -1;
+  // exactly zero: the sign at (py + e, pz + e^2)
+  if (Q[2] != P[2]) return Q[2] < P[2] ? 1 : -1;
+  if (Q[1] != P[1]) return Q[1] > P[1] ? 1 : -1;
+  return 0;  // the edge projects to a point
 }
 
-// 3. join the slices (one CTA per instance, shared memory over the compact
-//    slice roots): components with a border run are outside; the others are
-//    numbered (at most MAX_COMP get a winding-number seed); each compact root
-//    receives its final label.
-__global__ void __launch_bounds__(1024) k_join_cc(Inst* __restrict__ I) {
-  __shared__ int par[ROOT_CAP];
-  __shared__ unsigned flag[ROOT_CAP];
-  __shared__ int eoff[MAX_DIM + 1];
-  __shared__ int s_ncomp;
-  Inst& in = I[blockIdx.x];
-  if (in.err & ERR_DEGENERATE) return;
-  const int nz = in.dims[2];
-  const int nroots = nz * ROOTS_PER_SLICE;
-  if (in.err & ERR_RUNS) {
-    // too many slice components for the tables: every undecided cube becomes
-    // NEAR (exact: those elements take the exact test)
-    const int nx = in.dims[0], nrows = in.dims[1] * nz;
-    if (threadIdx.x == 0) { in.err |= ERR_RUNS; in.ncomp = 0; }
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
-      in.run_cnt[r] = 0;
-      uint8_t* row = in.cube + (long long)r * CUBE_PITCH;
-      for (int x = 0; x < nx; ++x) row[x] = CUBE_NEAR;
-    }
-    return;
-  }
-  if (threadIdx.x == 0) s_ncomp = 0;
-  for (int i = threadIdx.x; i < nroots; i += blockDim.x) {
-    par[i] = i;
-    // ids a slice did not use are marked outside so they are never numbered
-    flag[i] = (in.root_slot[i] < 0 || in.root_info[i]) ? RUN_OUT : 0u;
-  }
-  // per-slice edge counts (parallel loads), then their prefix from shared memory
-  for (int z = threadIdx.x; z < nz; z += blockDim.x) eoff[z + 1] = z ? in.zedge_cnt[z] : 0;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    eoff[0] = 0;
-    for (int z = 1; z <= nz; ++z) eoff[z] += eoff[z - 1];
-  }
-  __syncthreads();
-  // edges of all slices, flattened over the threads
-  for (int e = threadIdx.x; e < eoff[nz]; e += blockDim.x) {
-    int lo = 0, hi = nz - 1;
-    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (eoff[mid] <= e) lo = mid; else hi = mid - 1; }
-    const int z = lo, t = e - eoff[z];
-    // a: root slot of the run above; b: slot of the run below, whose slice
-    // root the lower slice recorded in run_par
-    int a = (int)in.run_flag[in.zedge[z * 2 * ZEDGE_CAP + 2 * t]];
-    int b = (int)in.run_flag[in.run_par[in.zedge[z * 2 * ZEDGE_CAP + 2 * t + 1]]];
-    uf_union(par, a, b);
-  }
-  __syncthreads();
-  {
-    // two-phase compression (ROOT_CAP <= 4 * blockDim)
-    static_assert(ROOT_CAP <= 4 * 1024, "four roots per thread");  // 48 x 82 = 3936
-    int rr[4];
-    for (int m = 0; m < 4; ++m) {
-      int i = threadIdx.x + m * blockDim.x;
-      rr[m] = i < nroots ? uf_root(par, i) : 0;
-    }
-    __syncthreads();
-    for (int m = 0; m < 4; ++m) {
-      int i = threadIdx.x + m * blockDim.x;
-      if (i >= nroots) continue;
-      par[i] = rr[m];
-      if ((flag[i] & RUN_OUT) && !(((volatile unsigned*)flag)[rr[m]] & RUN_OUT)) atomicOr(&flag[rr[m]], RUN_OUT);
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nroots; i += blockDim.x) {
-    if (par[i] != i || (flag[i] & RUN_OUT)) continue;
-    int c = atomicAdd(&s_ncomp, 1);
-    if (c < MAX_COMP) {
-      flag[i] |= (unsigned)c << 4;
-      int gs = in.root_slot[i];
-      in.comp_seed[c] = (gs / RUNS_PER_ROW) * CUBE_PITCH + (in.run_xx[gs] & 0xff);
-    } else {
-      flag[i] |= RUN_UNKNOWN;
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nroots; i += blockDim.x) in.root_label[i] = flag[par[i]];
-  if (threadIdx.x == 0) in.ncomp = s_ncomp;
+// exact sign of E(U->V; p): the FP64 static filter, else the expansion; both
+// from the lexicographically smaller end, so that the two orientations of an
+// edge give opposite signs
+__device__ __forceinline__ int edge_sign(const double* U, const double* V, double py, double pz) {
+  const bool uv = U[1] < V[1] || (U[1] == V[1] && (U[2] < V[2] || (U[2] == V[2] && U[0] < V[0])));
+  const double* P = uv ? U : V;
+  const double* Q = uv ? V : U;
+  const double t1 = __dmul_rn(__dsub_rn(Q[1], P[1]), __dsub_rn(pz, P[2]));
+  const double t2 = __dmul_rn(__dsub_rn(Q[2], P[2]), __dsub_rn(py, P[1]));
+  const double bound = 4.0 * 1.1102230246251565e-16 * (fabs(t1) + fabs(t2));
+  const double e = __dsub_rn(t1, t2);
+  int sg = e > bound ? 1 : (e < -bound ? -1 : edge_sign_exact(P, Q, py, pz));
+  return uv ? sg : -sg;
 }
 
-// 5. cube states of each row from its runs (16-byte stores)
-__global__ void k_run_states(Inst* __restrict__ I) {
+constexpr int ROW_UNDECIDED = 1 << 20;  // added to a row's crossing count when its list is full
+
+// one thread per surface triangle: its crossings with the row centre lines
+__global__ void __launch_bounds__(256) k_row_cross(Inst* __restrict__ I) {
   Inst& in = I[blockIdx.y];
-  if (in.err & ERR_DEGENERATE) return;
-  const int nrows = rows_of(in);
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
-    const int n = in.run_cnt[r];
-    if (!n) continue;  // all NEAR (or a row made NEAR in step 1)
-    unsigned w[CUBE_PITCH / 4];
-#pragma unroll
-    for (int i = 0; i < CUBE_PITCH / 4; ++i) w[i] = 0x02020202u;
-    for (int k = 0; k < n; ++k) {
-      int sl = r * RUNS_PER_ROW + k;
-      unsigned fl = in.root_label[in.run_flag[in.run_par[sl]]];
-      unsigned v = (fl & RUN_OUT) ? CUBE_OUT : ((fl & RUN_UNKNOWN) ? CUBE_NEAR : (CUBE_COMP0 + (fl >> 4)));
-      unsigned short xx = in.run_xx[sl];
-      int x0 = xx & 0xff, x1 = xx >> 8;
-#pragma unroll
-      for (int i = 0; i < CUBE_PITCH / 4; ++i) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          int x = 4 * i + b;
-          if (x >= x0 && x <= x1) w[i] = (w[i] & ~(0xffu << (8 * b))) | (v << (8 * b));
-        }
-      }
+  if (in.err & (ERR_DEGENERATE | ERR_NONFINITE)) return;
+  const int q = in.q, npf = (q + 1) * (q + 1), ntf = 2 * q * q;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long f = g / ntf;
+  if (f >= in.n_faces) return;
+  const int t = (int)(g - f * ntf);
+  const double* fn = in.surf + f * npf * 3;
+  const double* A = fn + 3 * c_ftri[q - 1][t][0];
+  const double* B = fn + 3 * c_ftri[q - 1][t][1];
+  const double* C = fn + 3 * c_ftri[q - 1][t][2];
+  const double ds = in.ds, oy = in.origin[1], oz = in.origin[2];
+  // float coordinates relative to A (each within u of its FP64 value)
+  const float by = (float)(B[1] - A[1]), bz = (float)(B[2] - A[2]), bx = (float)(B[0] - A[0]);
+  const float cy = (float)(C[1] - A[1]), cz = (float)(C[2] - A[2]), cx = (float)(C[0] - A[0]);
+  const float ay0 = (float)(A[1] - oy), az0 = (float)(A[2] - oz), ax0 = (float)(A[0] - in.origin[0]);
+  const float inv = in.inv_ds_f;
+  // rows whose centre may lie over the triangle's box: the float box and the
+  // scaling are within 4u (map extent) < 1e-4 cube of exact
+  const float ylo = ay0 + fminf(0.f, fminf(by, cy)), yhi = ay0 + fmaxf(0.f, fmaxf(by, cy));
+  const float zlo = az0 + fminf(0.f, fminf(bz, cz)), zhi = az0 + fmaxf(0.f, fmaxf(bz, cz));
+  const int y0 = max((int)ceilf(ylo * inv - 0.5f - 1e-4f), 0), y1 = min((int)floorf(yhi * inv - 0.5f + 1e-4f), in.dims[1] - 1);
+  const int z0 = max((int)ceilf(zlo * inv - 0.5f - 1e-4f), 0), z1 = min((int)floorf(zhi * inv - 0.5f + 1e-4f), in.dims[2] - 1);
+  const float u = 5.9604644775390625e-8f;
+  for (int kz = z0; kz <= z1; ++kz) {
+    const double pz = oz + ((double)kz + 0.5) * ds;
+    const float qz = (float)(pz - A[2]);
+    for (int ky = y0; ky <= y1; ++ky) {
+      const double py = oy + ((double)ky + 0.5) * ds;
+      const float qy = (float)(py - A[1]);
+      // float edge functions relative to A; each input is within u M of the
+      // exact difference, so |E_float - E| <= 64 u M^2
+      const float eab = by * qz - bz * qy;
+      const float ebc = (cy - by) * (qz - bz) - (cz - bz) * (qy - by);
+      const float eca = cz * qy - cy * qz;
+      const float M = fmaxf(fmaxf(fmaxf(fabsf(by), fabsf(bz)), fmaxf(fabsf(cy), fabsf(cz))), fmaxf(fabsf(qy), fabsf(qz)));
+      const float bnd = 64.0f * u * M * M;
+      int sab = eab > bnd ? 1 : (eab < -bnd ? -1 : 2);
+      int sbc = ebc > bnd ? 1 : (ebc < -bnd ? -1 : 2);
+      int sca = eca > bnd ? 1 : (eca < -bnd ? -1 : 2);
+      if ((sab == 1 || sbc == 1 || sca == 1) && (sab == -1 || sbc == -1 || sca == -1)) continue;  // outside
+      if (sab == 2) sab = edge_sign(A, B, py, pz);
+      if (sbc == 2) sbc = edge_sign(B, C, py, pz);
+      if (sca == 2) sca = edge_sign(C, A, py, pz);
+      if (sab == 0 || sab != sbc || sbc != sca) continue;
+      // crossing: x from the barycentric weights (clamped: a point of the
+      // triangle, so inside its face box and a NEAR cube)
+      const float s = (float)sab;
+      const float wa = fmaxf(s * ebc, 0.f), wb = fmaxf(s * eca, 0.f), wc = fmaxf(s * eab, 0.f);
+      const float wsum = wa + wb + wc;
+      const float xr = wsum > 0.f ? (wb * bx + wc * cx) / wsum : 0.f;
+      const int xc = clampi((int)floorf((ax0 + xr) * inv), 0, in.dims[0] - 1);
+      int* cnt = in.row_cnt + (kz * in.dims[1] + ky);
+      const int pos_k = atomicAdd(cnt, 1);
+      // all edge functions positive: the normal has x component > 0 and the
+      // line leaves the body here (-1); negative: it enters (+1)
+      if (pos_k < ROW_XCAP) in.row_x[(kz * in.dims[1] + ky) * ROW_XCAP + pos_k] = (xc << 1) | (sab > 0 ? 0 : 1);
+      else if (pos_k == ROW_XCAP) atomicAdd(cnt, ROW_UNDECIDED);
     }
-    uint4* row4 = reinterpret_cast<uint4*>(in.cube + (long long)r * CUBE_PITCH);
-#pragma unroll
-    for (int i = 0; i < CUBE_PITCH / 16; ++i) row4[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
   }
 }
 
-// winding number of each enclosed component's seed cube centre (FP32 solid
-// angles: the centre is >= ds/2 from every surface point, so the sum is far
-// from the 1/2 decision level)
-__global__ void k_winding(Inst* __restrict__ I) {
-  Inst& in = I[blockIdx.z];
-  const int k = blockIdx.y;
-  if (k >= min(in.ncomp, MAX_COMP) || (in.err & ERR_DEGENERATE)) return;
-  const int q = in.q, ntf = 2 * q * q, npf = (q + 1) * (q + 1);
-  long long ntri = in.n_faces * ntf;
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  float om = 0.0f;
-  if (t < ntri) {
-    int seed = in.comp_seed[k];
-    int row = seed / CUBE_PITCH, x = seed % CUBE_PITCH;
-    int y = row % in.dims[1], z = row / in.dims[1];
-    double P[3] = {in.origin[0] + (x + 0.5) * in.ds, in.origin[1] + (y + 0.5) * in.ds, in.origin[2] + (z + 0.5) * in.ds};
-    long long f = t / ntf;
-    int tt = (int)(t - f * ntf);
-    const double* fn = in.surf + f * npf * 3;
-    float v[3][3];
-    for (int c = 0; c < 3; ++c) {
-      int nd = c_ftri[q - 1][tt][c];
-      for (int a = 0; a < 3; ++a) v[c][a] = (float)(fn[3 * nd + a] - P[a]);
+// one warp per row: winding number of each cube that is not NEAR
+__global__ void __launch_bounds__(256) k_row_label(Inst* __restrict__ I) {
+  Inst& in = I[blockIdx.y];
+  if (in.err & (ERR_DEGENERATE | ERR_NONFINITE)) return;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nrows = in.dims[1] * in.dims[2];
+  if (r >= nrows) return;
+  const int cnt = in.row_cnt[r];
+  const bool undecided = cnt > ROW_XCAP;
+  if (undecided && lane == 0) atomicAdd(&in.rows_undecided, 1);
+  const int x0 = 4 * lane;
+  if (x0 >= in.dims[0]) return;
+  unsigned* word = reinterpret_cast<unsigned*>(in.cube + (long long)r * CUBE_PITCH + x0);
+  unsigned v = *word;
+  const int* xs = in.row_x + (long long)r * ROW_XCAP;
+  int w[4] = {0, 0, 0, 0};
+  if (!undecided)
+    for (int i = 0; i < cnt; ++i) {
+      const int e = xs[i], xc = e >> 1, d = (e & 1) ? 1 : -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] += xc < x0 + k ? d : 0;
     }
-    float la = sqrtf(v[0][0] * v[0][0] + v[0][1] * v[0][1] + v[0][2] * v[0][2]);
-    float lb = sqrtf(v[1][0] * v[1][0] + v[1][1] * v[1][1] + v[1][2] * v[1][2]);
-    float lc = sqrtf(v[2][0] * v[2][0] + v[2][1] * v[2][1] + v[2][2] * v[2][2]);
-    float cx = v[1][1] * v[2][2] - v[1][2] * v[2][1];
-    float cy = v[1][2] * v[2][0] - v[1][0] * v[2][2];
-    float cz = v[1][0] * v[2][1] - v[1][1] * v[2][0];
-    float det = v[0][0] * cx + v[0][1] * cy + v[0][2] * cz;
-    float ab = v[0][0] * v[1][0] + v[0][1] * v[1][1] + v[0][2] * v[1][2];
-    float ac = v[0][0] * v[2][0] + v[0][1] * v[2][1] + v[0][2] * v[2][2];
-    float bc = v[1][0] * v[2][0] + v[1][1] * v[2][1] + v[1][2] * v[2][2];
-    float den = la * lb * lc + ab * lc + ac * lb + bc * la;
-    om = 2.0f * atan2f(det, den);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (x0 + k >= in.dims[0]) break;
+    const unsigned b = (v >> (8 * k)) & 0xffu;
+    if (b == CUBE_NEAR) continue;
+    const unsigned st = undecided ? CUBE_NEAR : (w[k] == 0 ? CUBE_OUT : (w[k] == 1 ? CUBE_IN : CUBE_NEAR));
+    v = (v & ~(0xffu << (8 * k))) | (st << (8 * k));
   }
-  for (int s = 16; s; s >>= 1) om += __shfl_xor_sync(0xffffffffu, om, s);
-  __shared__ float ws[32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) ws[w] = om;
-  __syncthreads();
-  if (w == 0) {
-    float v = lane < (blockDim.x >> 5) ? ws[lane] : 0.0f;
-    for (int s = 16; s; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-    if (lane == 0) atomicAdd(&in.comp_w[k], v * (float)(0.25 / 3.14159265358979323846));
-  }
+  *word = v;
 }
 
 // ------------------------------------------------------------------ a4: classify + compact
@@ -699,11 +479,8 @@ __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const lo
               uint8_t s = row[x];
               if (s == CUBE_OUT) {
                 any_out = true;
-              } else if (s >= CUBE_COMP0 && s < CUBE_COMP0 + MAX_COMP) {
-                float w = in.comp_w[s - CUBE_COMP0];
-                if (w > 0.75f && w < 1.25f) any_in = true;
-                else if (w > -0.25f && w < 0.25f) any_out = true;
-                else { any_near = true; break; }
+              } else if (s == CUBE_IN) {
+                any_in = true;
               } else {
                 any_near = true;
                 break;

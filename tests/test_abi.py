@@ -54,7 +54,7 @@ def test_struct_layouts_match_header(tmp_path):
         "F(dc_config,holemap_cells); F(dc_config,bin_cubes); F(dc_config,max_inflight); F(dc_config,profile);\n"
         "S(dc_request); F(dc_request,q); F(dc_request,n_faces); F(dc_request,face_nodes); F(dc_request,pose);\n"
         "F(dc_request,flags_out); F(dc_request,dist_out); F(dc_request,on_device); F(dc_request,async); F(dc_request,stream);\n"
-        "S(dc_stats); F(dc_stats,holemap_components); F(dc_stats,ms_surface); F(dc_stats,ms_total);\n"
+        "S(dc_stats); F(dc_stats,holemap_rows_undecided); F(dc_stats,ms_surface); F(dc_stats,ms_total);\n"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)

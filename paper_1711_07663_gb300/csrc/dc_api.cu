@@ -145,21 +145,15 @@ struct LaunchParams {
   Inst* d_inst = nullptr;
   long long* d_off = nullptr;
   unsigned long long *cand = nullptr, *redo = nullptr, *d_cnt = nullptr;
-  // flags-only split of the exact stage (k_near1..3), when some instance
+  // flags-only form of the exact stage (k_near_*), when some instance
   // asks for flags only
   bool near = false;
-  unsigned* status = nullptr;
-  unsigned long long *task = nullptr, *full = nullptr, *pair = nullptr, *f64 = nullptr;
-  unsigned long long task_cap = 0, pair_cap = 0, f64_cap = 0;
-  float* tface = nullptr;
-  int tstride = 0;
+  unsigned long long* full = nullptr;
   bool operator==(const LaunchParams& o) const {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
            pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
-           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && status == o.status &&
-           task == o.task && full == o.full && task_cap == o.task_cap && pair == o.pair && pair_cap == o.pair_cap &&
-           tface == o.tface && tstride == o.tstride && f64 == o.f64 && f64_cap == o.f64_cap;
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && full == o.full;
   }
 };
 
@@ -208,9 +202,9 @@ struct Slot {
 };
 
 constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters,
-                          // [11] near tasks, [12] holes decided by the hole map,
-                          // [13] near pairs, [14,15] full-search list/cursor,
-                          // [16] near pairs given the full FP32 test, [17] near FP64 list
+                          // [11] near faces tested, [12] holes decided by the hole map,
+                          // [14,15] full-search list/cursor, [16] near pairs given the
+                          // full FP32 test
 
 }  // namespace
 
@@ -264,12 +258,6 @@ void launch_rows(Inst* d_inst, int n, long long max_tri, cudaStream_t st) {
   k_row_label<<<dim3((MAX_DIM * MAX_DIM + 7) / 8, n), 256, 0, st>>>(d_inst);
 }
 
-// (element, face) task capacity of the flags-only split; elements that find
-// it full fall back to the full search
-unsigned long long near_task_cap(long long ne_total) { return (unsigned long long)ne_total + 65536ull; }
-unsigned long long near_pair_cap(long long ne_total) { return 8ull * (unsigned long long)ne_total + 262144ull; }
-unsigned long long near_f64_cap(long long ne_total) { return (unsigned long long)ne_total / 8ull + 65536ull; }
-
 // bytes of arena a batch needs
 size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
   size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
@@ -283,13 +271,7 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
          run_bytes();
   }
   s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
-  int qmax = 1;
-  for (auto& r : v) qmax = std::max(qmax, (int)r.req->q);
-  s += al256(sizeof(unsigned) * ne_total) + al256(sizeof(unsigned long long) * near_task_cap(ne_total)) +
-       al256(sizeof(float) * 3 * (qmax + 1) * (qmax + 1) * near_task_cap(ne_total)) +
-       al256(sizeof(unsigned long long) * near_pair_cap(ne_total)) +
-       al256(sizeof(unsigned long long) * near_f64_cap(ne_total)) +
-       al256(sizeof(unsigned long long) * ne_total);  // near status, tasks, task faces, pairs, full-search list
+  s += al256(sizeof(unsigned long long) * ne_total);  // full-search list of the flags-only stage
   s += al256(sizeof(unsigned long long) * NCNT);
   s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
   return s;
@@ -411,7 +393,7 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
   if (prof) CK(record(s.ev[2], st, capturing));
   CandList cl{cand, (unsigned long long)ne_total, d_cnt};
   CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
-  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl, d_cnt + 12);
+  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl, d_cnt);
   if (prof) CK(record(s.ev[3], st, capturing));
   const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
   const int WPB = TB / 32;
@@ -424,13 +406,12 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     occ = std::max(occ, 1);
     if (P.near) {
       CandList fl{P.full, (unsigned long long)ne_total, d_cnt + 14};
-      NearBufs nb{P.status, P.task, P.task_cap, P.pair, P.pair_cap, P.tface, P.tstride, P.f64, P.f64_cap, d_cnt + 11};
-      k_near1<<<c->n_sm * 8, TB, 0, st>>>(d_inst, cl, fl, nb, d_cnt + 4);
-      k_near_pairs<<<c->n_sm * 6, TB, 0, st>>>(d_inst, cl, nb, d_cnt + 4);
-      k_near_cross<<<c->n_sm * 4, TB, 0, st>>>(d_inst, cl, nb);
-      k_near_eval<<<c->n_sm * 2, TB, 0, st>>>(d_inst, cl, nb, d_cnt + 4);
-      k_near_fp64<<<c->n_sm, TB, 0, st>>>(d_inst, cl, nb, d_cnt + 4);
-      k_near3<<<c->n_sm * 4, TB, 0, st>>>(d_inst, cl, fl, nb, d_cnt + 4);
+      NearBufs nb{d_cnt + 11};
+      const NearLayout Ln = near_layout(pmax, qmax);
+      int occn = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, TB, (size_t)Ln.total * WPB);
+      occn = std::max(occn, 1);
+      k_near_main<<<c->n_sm * occn, TB, (size_t)Ln.total * WPB, st>>>(d_inst, cl, fl, nb, pmax, qmax, d_cnt + 4);
       k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, fl, rl, pmax, qmax, d_cnt + 4);
     } else {
       k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
@@ -558,12 +539,6 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
-  unsigned* nstatus = (unsigned*)take(sizeof(unsigned) * ne_total);
-  unsigned long long* ntask = (unsigned long long*)take(sizeof(unsigned long long) * near_task_cap(ne_total));
-  unsigned long long* npair = (unsigned long long*)take(sizeof(unsigned long long) * near_pair_cap(ne_total));
-  const int tstride = 3 * (qmax + 1) * (qmax + 1);
-  float* ntface = (float*)take(sizeof(float) * tstride * near_task_cap(ne_total));
-  unsigned long long* nf64 = (unsigned long long*)take(sizeof(unsigned long long) * near_f64_cap(ne_total));
   unsigned long long* nfull = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   int8_t* oflags = (int8_t*)take(ne_total);
   double* odist = (double*)take(sizeof(double) * ne_total);
@@ -595,10 +570,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     bool flags_only = false;
     for (auto& r : v) flags_only |= r.req->dist_out == nullptr;
     lp.near = c->cfg.precision == DC_FP32_RECHECK && flags_only && ne_total < (1LL << 31);
-    lp.status = nstatus; lp.task = ntask; lp.full = nfull; lp.task_cap = near_task_cap(ne_total);
-    lp.pair = npair; lp.pair_cap = near_pair_cap(ne_total);
-    lp.tface = ntface; lp.tstride = tstride;
-    lp.f64 = nf64; lp.f64_cap = near_f64_cap(ne_total);
+    lp.full = nfull;
   }
   {
     const ExLayout Ld = ex_layout(pmax, qmax, 8);
@@ -637,7 +609,7 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
   S.pairs_recheck = (int64_t)s.h_cnt[6];
   S.n_fringe = (int64_t)s.h_cnt[7];
   S.n_hole = (int64_t)(s.h_cnt[8] + s.h_cnt[12]);
-  S.n_field = S.n_elem - S.n_candidates - (int64_t)s.h_cnt[12] + (int64_t)s.h_cnt[9];
+  S.n_field = S.n_elem - S.n_fringe - S.n_hole;
   S.fallbacks = (int64_t)s.h_cnt[10];
   S.near_tasks = s.near ? (int64_t)s.h_cnt[11] : 0;
   S.n_full_search = s.near ? (int64_t)s.h_cnt[14] : (int64_t)s.h_cnt[0];
@@ -769,8 +741,12 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     cudaFuncAttributes fe, fd;
     if (cudaFuncGetAttributes(&fe, k_exact<float>) != cudaSuccess || cudaFuncGetAttributes(&fd, k_exact<double>) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
+    cudaFuncAttributes fnm;
+    if (cudaFuncGetAttributes(&fnm, k_near_main) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
     if (cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fe.sharedSizeBytes)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_near_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(c->smem_optin - fnm.sharedSizeBytes)) != cudaSuccess ||
         cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fd.sharedSizeBytes)) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
@@ -1104,7 +1080,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CandList cl{cand, (unsigned long long)n_elem, d_cnt};
   CandList rl{redo, (unsigned long long)n_elem, d_cnt + 2};
   CandList none{redo, 0, d_cnt + 2};
-  k_classify<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(d_inst, d_off + 2, 1, n_elem, cl, d_cnt + 12);
+  k_classify<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(d_inst, d_off + 2, 1, n_elem, cl, d_cnt);
   const ExLayout Lf = ex_layout(p, q, 4), Ld = ex_layout(p, q, 8);
   const int WPB = TB / 32;
   if ((long long)Ld.total * WPB > D.smem_optin)

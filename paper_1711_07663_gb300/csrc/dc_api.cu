@@ -251,10 +251,32 @@ size_t run_bytes() {
   return al256(sizeof(int) * rows) + al256(sizeof(int) * rows * ROW_XCAP);
 }
 
-// inside/outside of the hole-map cubes: row crossings, then row labels
-void launch_rows(Inst* d_inst, int n, long long max_tri, cudaStream_t st) {
-  k_row_cross<<<dim3((unsigned)((max_tri + 255) / 256), n), 256, 0, st>>>(d_inst);
-  k_row_label<<<dim3((MAX_DIM * MAX_DIM + 7) / 8, n), 256, 0, st>>>(d_inst);
+// Launch k on st; with pdl, as a programmatic dependent launch: it may start
+// while the previous kernel of the stream finishes, its pdl_enter() waiting for
+// that kernel's completion (captured into graphs as programmatic edges).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// face bins filled and row crossings found (one launch), then row labels
+cudaError_t launch_rows(bool pdl, Inst* d_inst, const long long* foff, int n, long long nf_total, long long max_tri,
+                        cudaStream_t st) {
+  const int fill_blocks = (int)((nf_total + 255) / 256);
+  cudaError_t e = launch_k(pdl, k_fill_cross, dim3((unsigned)(fill_blocks + (max_tri + 255) / 256), n), dim3(256), 0,
+                           st, d_inst, foff, n, nf_total, fill_blocks);
+  if (e != cudaSuccess) return e;
+  return launch_k(pdl, k_row_label, dim3((MAX_DIM * MAX_DIM + 7) / 8, n), dim3(256), 0, st, d_inst);
 }
 
 // bytes of arena a batch needs
@@ -381,17 +403,17 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
 
   const int TB = 256;
   unsigned gf = (unsigned)((nf_total + TB - 1) / TB);
-  k_surface<<<dim3((unsigned)((P.max_f + SURF_FPB - 1) / SURF_FPB), n), TB, 0, st>>>(d_inst);
-  k_clear<<<dim3(64, n), TB, 0, st>>>(d_inst);
-  k_tag<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
-  k_bin_scan<<<n, 1024, 0, st>>>(d_inst);
-  k_bin_fill<<<gf, TB, 0, st>>>(d_inst, foff, n, nf_total);
+  CK(launch_k(false, k_surface, dim3((unsigned)((P.max_f + SURF_FPB - 1) / SURF_FPB), n), dim3(TB), 0, st, d_inst));
+  CK(launch_k(true, k_clear, dim3(64, n), dim3(TB), 0, st, d_inst));
+  CK(launch_k(true, k_tag, dim3(gf), dim3(TB), 0, st, d_inst, foff, n, nf_total));
+  CK(launch_k(true, k_bin_scan, dim3(n), dim3(1024), 0, st, d_inst));
   if (prof) CK(record(s.ev[1], st, capturing));
-  launch_rows(d_inst, n, max_tri, st);
+  CK(launch_rows(true, d_inst, foff, n, nf_total, max_tri, st));
   if (prof) CK(record(s.ev[2], st, capturing));
   CandList cl{cand, (unsigned long long)ne_total, d_cnt};
   CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
-  k_classify<<<(unsigned)((ne_total + TB - 1) / TB), TB, 0, st>>>(d_inst, eoff, n, ne_total, cl, d_cnt);
+  CK(launch_k(true, k_classify, dim3((unsigned)((ne_total + TB - 1) / TB)), dim3(TB), 0, st, d_inst, eoff, n, ne_total,
+              cl, d_cnt));
   if (prof) CK(record(s.ev[3], st, capturing));
   const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
   const int WPB = TB / 32;
@@ -406,22 +428,25 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     int occn = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, TB, sm);
     occn = std::max(occn, 1);
-    k_near_main<<<c->n_sm * occn, TB, sm, st>>>(d_inst, cl, nb, pmax, qmax, d_cnt + 4);
+    CK(launch_k(true, k_near_main, dim3(c->n_sm * occn), dim3(TB), sm, st, d_inst, cl, nb, pmax, qmax, d_cnt + 4));
     if (prof) CK(record(s.ev[5], st, capturing));
   } else if (P.precision == DC_FP32_RECHECK) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);
     occ = std::max(occ, 1);
-    k_exact<float><<<c->n_sm * occ, TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, pmax, qmax, d_cnt + 4);
+    CK(launch_k(true, k_exact<float>, dim3(c->n_sm * occ), dim3(TB), (size_t)Lf.total * WPB, st, d_inst, cl, rl, pmax,
+                qmax, d_cnt + 4));
     if (prof) CK(record(s.ev[5], st, capturing));
     // the FP64 redo pass is rarely non-empty: a small persistent grid keeps
     // its launch cheap
-    k_exact<double><<<std::min(c->n_sm, 16), TB, (size_t)Ld.total * WPB, st>>>(d_inst, rl, none, pmax, qmax, d_cnt + 4);
+    CK(launch_k(true, k_exact<double>, dim3(std::min(c->n_sm, 16)), dim3(TB), (size_t)Ld.total * WPB, st, d_inst, rl,
+                none, pmax, qmax, d_cnt + 4));
   } else {
     int occd = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB);
     occd = std::max(occd, 1);
-    k_exact<double><<<c->n_sm * occd, TB, (size_t)Ld.total * WPB, st>>>(d_inst, cl, none, pmax, qmax, d_cnt + 4);
+    CK(launch_k(true, k_exact<double>, dim3(c->n_sm * occd), dim3(TB), (size_t)Ld.total * WPB, st, d_inst, cl, none,
+                pmax, qmax, d_cnt + 4));
     if (prof) CK(record(s.ev[5], st, capturing));
   }
   if (prof) CK(record(s.ev[4], st, capturing));
@@ -1070,8 +1095,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);
   k_tag<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
   k_bin_scan<<<1, 1024, 0, st>>>(d_inst);
-  k_bin_fill<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
-  launch_rows(d_inst, 1, n_faces * 2LL * q * q, st);
+  CK(launch_rows(false, d_inst, d_off, 1, n_faces, n_faces * 2LL * q * q, st));
   CandList cl{cand, (unsigned long long)n_elem, d_cnt};
   CandList rl{redo, (unsigned long long)n_elem, d_cnt + 2};
   CandList none{redo, 0, d_cnt + 2};

@@ -91,6 +91,15 @@ struct Inst {
 };
 
 // ---------------------------------------------------------------- helpers
+// Programmatic dependent launch: a kernel of the cut waits here until the
+// kernel before it has completed and its writes are visible (a no-op when it
+// was launched without the programmatic attribute), then lets the next kernel
+// be launched, so that launch overlaps this kernel's run.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned long long dkey(double d) {
   unsigned long long b = (unsigned long long)__double_as_longlong(d);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);

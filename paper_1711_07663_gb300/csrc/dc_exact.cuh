@@ -874,6 +874,7 @@ __device__ bool process_element(WarpCtx<T>& W, WarpState<T>& S, ExCounters& cnt)
 template <class T>
 __global__ void __launch_bounds__(256, 2) k_exact(Inst* __restrict__ I, CandList cl, CandList redo, int pmax, int qmax,
                                                   unsigned long long* __restrict__ gcnt) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, Cand
   __shared__ unsigned char s_et[MAX_P][MAX_NTE][3], s_ft[MAX_Q][MAX_NTF][3];
   for (int i = threadIdx.x; i < (int)sizeof(s_et); i += blockDim.x) (&s_et[0][0][0])[i] = (&c_etri[0][0][0])[i];
   for (int i = threadIdx.x; i < (int)sizeof(s_ft); i += blockDim.x) (&s_ft[0][0][0])[i] = (&c_ftri[0][0][0])[i];
+  pdl_enter();
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const NearLayout Lo = near_layout(pmax, qmax);

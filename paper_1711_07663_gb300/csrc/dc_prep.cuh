@@ -67,6 +67,7 @@ __device__ void grid_from_box(Inst& in) {
 // (face, axis) takes the face's box from shared memory; the last block of an
 // instance to finish derives its hole-map grid.
 __global__ void __launch_bounds__(256) k_surface(Inst* __restrict__ I) {
+  pdl_enter();
   __shared__ double s_x[SURF_FPB * MAX_NPF * 3];
   __shared__ unsigned long long s_key[6];
   __shared__ unsigned s_ext[3];
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(256) k_surface(Inst* __restrict__ I) {
 }
 
 __global__ void k_clear(Inst* __restrict__ I) {
+  pdl_enter();
   Inst& in = I[blockIdx.y];
   long long ncube = (long long)in.dims[1] * in.dims[2] * CUBE_PITCH;
   int nb = in.bdims[0] * in.bdims[1] * in.bdims[2];
@@ -171,6 +173,7 @@ __device__ __forceinline__ int cube_floorf(float x, int n) {
 
 // a3: NEAR tags of the hole map, and face -> bin (bin of the box's min corner)
 __global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total) {
+  pdl_enter();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nf_total) return;
   int ii = find_inst(foff, n_inst, g);
@@ -200,37 +203,73 @@ __global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, 
   atomicAdd(&in.bin_cnt[bi], 1);
 }
 
-// exclusive scan of the bin counts (one CTA per instance); counts become cursors
-__global__ void k_bin_scan(Inst* __restrict__ I) {
-  __shared__ int sums[1024];
+// exclusive scan of the bin counts (one CTA of 1024 threads per instance):
+// thread t takes the t-th chunk of consecutive bins (held in registers when a
+// chunk has at most BIN_PER_T bins, else read twice), the CTA scans the chunk
+// totals with warp shuffles; counts become cursors
+constexpr int BIN_PER_T = 10;
+__global__ void __launch_bounds__(1024) k_bin_scan(Inst* __restrict__ I) {
+  pdl_enter();
+  __shared__ int wsum[32];
   Inst& in = I[blockIdx.x];
-  int nb = in.bdims[0] * in.bdims[1] * in.bdims[2];
+  const int nb = in.bdims[0] * in.bdims[1] * in.bdims[2];
   if ((in.err & ERR_DEGENERATE) || nb > in.nbins_cap) return;
-  int t = threadIdx.x, T = blockDim.x;
-  int chunk = (nb + T - 1) / T;
-  int b0 = min(t * chunk, nb), b1 = min(b0 + chunk, nb);
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, T = blockDim.x;
+  const int chunk = (nb + T - 1) / T;
+  const int b0 = min(t * chunk, nb), b1 = min(b0 + chunk, nb);
+  int c[BIN_PER_T];
   int s = 0;
-  for (int k = b0; k < b1; ++k) s += in.bin_cnt[k];
-  sums[t] = s;
+  if (chunk <= BIN_PER_T) {
+#pragma unroll
+    for (int k = 0; k < BIN_PER_T; ++k) {
+      c[k] = b0 + k < b1 ? in.bin_cnt[b0 + k] : 0;
+      s += c[k];
+    }
+  } else {
+    for (int k = b0; k < b1; ++k) s += in.bin_cnt[k];
+  }
+  // inclusive scan of the chunk totals: within the warp, then over warps
+  int x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += v;
+  }
+  if (lane == 31) wsum[wid] = x;
   __syncthreads();
-  for (int off = 1; off < T; off <<= 1) {
-    int v = (t >= off) ? sums[t - off] : 0;
-    __syncthreads();
-    sums[t] += v;
-    __syncthreads();
+  if (wid == 0) {
+    int y = lane < (T >> 5) ? wsum[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, y, d);
+      if (lane >= d) y += v;
+    }
+    wsum[lane] = y;
   }
-  int run = sums[t] - s;
-  for (int k = b0; k < b1; ++k) {
-    int c = in.bin_cnt[k];
-    in.bin_off[k] = run;
-    run += c;
-    in.bin_cnt[k] = 0;
+  __syncthreads();
+  int run = x - s + (wid > 0 ? wsum[wid - 1] : 0);
+  if (chunk <= BIN_PER_T) {
+#pragma unroll
+    for (int k = 0; k < BIN_PER_T; ++k) {
+      if (b0 + k < b1) {
+        in.bin_off[b0 + k] = run;
+        in.bin_cnt[b0 + k] = 0;
+      }
+      run += c[k];
+    }
+  } else {
+    for (int k = b0; k < b1; ++k) {
+      const int v = in.bin_cnt[k];
+      in.bin_off[k] = run;
+      in.bin_cnt[k] = 0;
+      run += v;
+    }
   }
-  if (t == T - 1) in.bin_off[nb] = sums[t];
+  if (t == T - 1) in.bin_off[nb] = wsum[(T >> 5) - 1];
 }
 
-__global__ void k_bin_fill(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total) {
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bin_fill(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst,
+                                         long long nf_total, long long g) {
   if (g >= nf_total) return;
   int ii = find_inst(foff, n_inst, g);
   Inst& in = I[ii];
@@ -330,11 +369,9 @@ __device__ __forceinline__ int edge_sign(const double* U, const double* V, doubl
 constexpr int ROW_UNDECIDED = 1 << 20;  // added to a row's crossing count when its list is full
 
 // one thread per surface triangle: its crossings with the row centre lines
-__global__ void __launch_bounds__(256) k_row_cross(Inst* __restrict__ I) {
-  Inst& in = I[blockIdx.y];
+__device__ __forceinline__ void row_cross(Inst& in, long long g) {
   if (in.err & (ERR_DEGENERATE | ERR_NONFINITE)) return;
   const int q = in.q, npf = (q + 1) * (q + 1), ntf = 2 * q * q;
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long f = g / ntf;
   if (f >= in.n_faces) return;
   const int t = (int)(g - f * ntf);
@@ -393,8 +430,22 @@ __global__ void __launch_bounds__(256) k_row_cross(Inst* __restrict__ I) {
   }
 }
 
+// face -> bin fill (blocks [0, fill_blocks), one thread per face over all
+// instances) and row crossings (the other blocks, one thread per triangle of
+// instance blockIdx.y): both read only what the earlier kernels wrote
+__global__ void __launch_bounds__(256) k_fill_cross(Inst* __restrict__ I, const long long* __restrict__ foff,
+                                                    int n_inst, long long nf_total, int fill_blocks) {
+  pdl_enter();
+  if ((int)blockIdx.x < fill_blocks) {
+    if (blockIdx.y == 0) bin_fill(I, foff, n_inst, nf_total, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    return;
+  }
+  row_cross(I[blockIdx.y], (long long)(blockIdx.x - fill_blocks) * blockDim.x + threadIdx.x);
+}
+
 // one warp per row: winding number of each cube that is not NEAR
 __global__ void __launch_bounds__(256) k_row_label(Inst* __restrict__ I) {
+  pdl_enter();
   Inst& in = I[blockIdx.y];
   if (in.err & (ERR_DEGENERATE | ERR_NONFINITE)) return;
   const int lane = threadIdx.x & 31;
@@ -458,6 +509,7 @@ __device__ __forceinline__ int point_label(const Inst& in, float x, float y, flo
 __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const long long* __restrict__ eoff, int n_inst,
                                                   long long ne_total, CandList cl,
                                                   unsigned long long* __restrict__ cnt) {
+  pdl_enter();
   const unsigned FULL = 0xffffffffu;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = g < ne_total;

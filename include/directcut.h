@@ -88,7 +88,8 @@ typedef struct {
     size_t mem_budget_bytes;  /* device bytes the context may hold; 0 = no limit */
     double tol;               /* fringe tolerance, absolute mesh units; 0 -> 1e-7 (Alg. cp1) */
     int32_t holemap_cells;    /* hole-map cubes along the longest surface side, 8..80;
-                                 0 -> 64 (the paper uses 60-80) */
+                                 0 -> automatic: about 1.8 cubes per mean element edge of
+                                 the cut grid, 16..80 (the paper uses 60-80) */
     int32_t bin_cubes;        /* hole-map cubes per face bin along each axis, 1..16; 0 -> 4 */
     int32_t max_inflight;     /* serving slots for dc_submit, 1..64; 0 -> 4 */
     int32_t profile;          /* 1: time each phase with CUDA events (dc_get_stats) */

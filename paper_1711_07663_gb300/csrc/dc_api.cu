@@ -49,8 +49,23 @@ dc_status fail(dc_status st, const char* fmt, ...) {
 // the exact test: origin at the centre of the float box, node coordinates
 // relative to it rounded to float (the values every exact-test kernel uses).
 __global__ void k_elem_box(const double* __restrict__ nodes, long long n_elem, int npe, float* __restrict__ box,
-                           float* __restrict__ loc, double* __restrict__ org, int* __restrict__ bad) {
+                           float* __restrict__ loc, double* __restrict__ org, int* __restrict__ bad,
+                           double* __restrict__ ext_sum) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ext_sum) {
+    // sum of the elements' longest box sides (warp sums, then one atomic each)
+    double ext = 0.0;
+    if (e < n_elem) {
+      const double* y = nodes + e * npe * 3;
+      double lo[3] = {y[0], y[1], y[2]}, hi[3] = {y[0], y[1], y[2]};
+      for (int k = 1; k < npe; ++k)
+        for (int a = 0; a < 3; ++a) { lo[a] = fmin(lo[a], y[3 * k + a]); hi[a] = fmax(hi[a], y[3 * k + a]); }
+      ext = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
+      if (!(ext < 1e300)) ext = 0.0;
+    }
+    for (int s = 16; s; s >>= 1) ext += __shfl_xor_sync(0xffffffffu, ext, s);
+    if ((threadIdx.x & 31) == 0 && ext > 0.0) atomicAdd(ext_sum, ext);
+  }
   if (e >= n_elem) return;
   const double* x = nodes + e * npe * 3;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -127,6 +142,7 @@ struct Mesh {
   float* box = nullptr;
   float* loc = nullptr;    // element-frame node coordinates [n_elem][3][npe]
   double* org = nullptr;   // element frame origins [n_elem][3]
+  float h_elem = 0.f;      // mean longest box side of the elements
 };
 
 struct Arena {
@@ -548,6 +564,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.tol = c->cfg.tol;
     in.tol_f = float_up(c->cfg.tol);
     in.holemap_cells = c->cfg.holemap_cells;
+    in.h_elem = m.h_elem;
     in.bin_cubes = c->cfg.bin_cubes;
     in.want_dist = r->dist_out ? 1 : 0;
     for (int a = 0; a < 3; ++a) { in.sbox_key[a] = ~0ULL; in.sbox_key[3 + a] = 0ULL; }
@@ -710,7 +727,7 @@ dc_status dc_config_default(dc_config* cfg) {
   cfg->device = 0;
   cfg->precision = DC_FP32_RECHECK;
   cfg->tol = 1e-7;
-  cfg->holemap_cells = 64;
+  cfg->holemap_cells = 0;
   cfg->bin_cubes = 4;
   cfg->max_inflight = 4;
   return DC_OK;
@@ -723,11 +740,11 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
   dc_config cfg;
   if (cfg_in) cfg = *cfg_in; else dc_config_default(&cfg);
   if (cfg.tol == 0.0) cfg.tol = 1e-7;
-  if (cfg.holemap_cells == 0) cfg.holemap_cells = 64;
   if (cfg.bin_cubes == 0) cfg.bin_cubes = 4;
   if (cfg.max_inflight == 0) cfg.max_inflight = 4;
   if (!(cfg.tol > 0.0) || !std::isfinite(cfg.tol)) return fail(DC_EINVAL, "tol must be positive and finite");
-  if (cfg.holemap_cells < 8 || cfg.holemap_cells > MAX_CELLS) return fail(DC_EINVAL, "holemap_cells outside 8..%d", MAX_CELLS);
+  if (cfg.holemap_cells != 0 && (cfg.holemap_cells < 8 || cfg.holemap_cells > MAX_CELLS))
+    return fail(DC_EINVAL, "holemap_cells outside 8..%d (or 0: automatic)", MAX_CELLS);
   if (cfg.bin_cubes < 1 || cfg.bin_cubes > 16) return fail(DC_EINVAL, "bin_cubes outside 1..16");
   if (cfg.max_inflight < 1 || cfg.max_inflight > 64) return fail(DC_EINVAL, "max_inflight outside 1..64");
   if (cfg.precision != DC_FP64 && cfg.precision != DC_FP32_RECHECK) return fail(DC_EINVAL, "unknown precision %d", cfg.precision);
@@ -776,8 +793,9 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     dc_status st = init_slot(s, cfg.profile);
     if (st) return bail(st);
   }
-  int* d_bad = nullptr;
-  if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  int* d_bad = nullptr;  // [0]: a node is not finite; bytes 8..15: sum of element extents
+  if (cudaMalloc(&d_bad, 16) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  double* d_ext = reinterpret_cast<double*>(reinterpret_cast<char*>(d_bad) + 8);
   cudaStream_t st = c->slots[0].stream;
   c->meshes.resize(n_meshes);
   for (int i = 0; i < n_meshes; ++i) {
@@ -805,11 +823,13 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
       cudaFree(d_bad);
       return bail(fail(DC_ECUDA, "mesh %d: copying nodes failed", i));
     }
-    cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+    cudaMemsetAsync(d_bad, 0, 16, st);
     k_elem_box<<<(unsigned)((md.n_elem + 255) / 256), 256, 0, st>>>(m.nodes, md.n_elem, (int)npe, m.box, m.loc, m.org,
-                                                                      d_bad);
+                                                                      d_bad, d_ext);
     int bad = 0;
+    double ext = 0.0;
     if (cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&ext, d_ext, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       cudaFree(d_bad);
       return bail(fail(DC_ECUDA, "mesh %d: element boxes failed: %s", i, cudaGetErrorString(cudaGetLastError())));
@@ -818,6 +838,7 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
       cudaFree(d_bad);
       return bail(fail(DC_EINVAL, "mesh %d has a NaN or infinite node", i));
     }
+    m.h_elem = (float)(ext / (double)md.n_elem);
   }
   cudaFree(d_bad);
   *out = c;
@@ -1089,7 +1110,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
   CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
   const int TB = 256;
-  k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, nullptr, nullptr, d_bad);
+  k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, nullptr, nullptr, d_bad, nullptr);
   unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
   k_surface<<<dim3((unsigned)((n_faces + SURF_FPB - 1) / SURF_FPB), 1), TB, 0, st>>>(d_inst);
   k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);

@@ -69,7 +69,8 @@ struct Inst {
   // parameters
   double tol;
   float tol_f;             // tol rounded up to float
-  int holemap_cells;
+  int holemap_cells;        // 0: automatic, from h_elem
+  float h_elem;             // mean longest box side of the grid's elements
   int bin_cubes;
   int want_dist;
   // derived on the device

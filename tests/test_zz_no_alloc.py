@@ -40,7 +40,9 @@ def test_noalloc_matches_dc_cut_on_two_calls_in_a_row():
     faces = torch.from_numpy(case.faces).to(dev)
     poses = [None, np.concatenate([W.random_rotation(W.rng(4)), np.array([[0.05], [-0.08], [0.02]])], axis=1)]
     h = 4.0 / case.n
-    with dc.Context([(case.p, nodes)]) as ctx:
+    # the same hole-map resolution as the allocation-free cut (64 cubes), so
+    # that the same elements are settled by the map (their distances are +-inf)
+    with dc.Context([(case.p, nodes)], holemap_cells=64) as ctx:
         for pose in poses:  # two calls in a row share the library's scratch array
             f_ref = torch.empty(case.n_elem, dtype=torch.int8, device=dev)
             d_ref = torch.empty(case.n_elem, dtype=torch.float64, device=dev)

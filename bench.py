@@ -293,6 +293,33 @@ def run_ours(args, world, rank, local):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
     e2e_same = bool(torch.equal(flags_h, flags.cpu()))
 
+    # the unblank step of a moving grid (two cuts of the resident grid, at t and
+    # t + dt, in one batched call, then the set logic), overset kind
+    ft = torch.empty_like(flags)
+    ftp = torch.empty_like(flags)
+    ib_prev = torch.ones_like(flags)
+    ib = torch.empty_like(flags)
+    unb = torch.empty(NE, dtype=torch.uint8, device=dev)
+    import workloads as Wl
+    def step_poses(k):
+        return [np.concatenate([Wl.axis_rotation([0.2, 0.9, 0.4], np.deg2rad(0.5 * (k + j))), np.zeros((3, 1))], axis=1)
+                for j in (0, 1)]
+    ub_ms = []
+    for k in range(8 + args.warmup):
+        pt, ptp = step_poses(k)
+        flush.fill_(k & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.cut_batch([0, 0], [dict(q=case.q, faces=faces, flags_out=ft, pose=pt),
+                               dict(q=case.q, faces=faces, flags_out=ftp, pose=ptp)])
+        dc.dc_unblank(dc.DC_OVERSET, ib_prev, ft, ftp, ib, unb, stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ib_prev, ib = ib, ib_prev
+        if k >= args.warmup:
+            ub_ms.append(a.elapsed_time(b))
+
     # roofline of the dominant kernel (the flags-only exact stage): ALU bound;
     # every listed pair takes the separation test, the rest the full test
     ex_ms = float(np.mean(exact_ms))
@@ -321,6 +348,7 @@ def run_ours(args, world, rank, local):
             "cut_ms_p50": float(np.percentile(step_ms, 50)), "cut_ms_p99": float(np.percentile(step_ms, 99)),
             "plain_fp64_ms": plain_ms, "speedup_vs_plain": (plain_ms / float(np.median(step_ms))) if plain_ms else None,
             "plain_same_flags": same_flags,
+            "unblank_step_ms": float(np.median(ub_ms)),
             "phases_ms": {"surface_bins": float(np.mean(surf_ms)), "holemap": float(np.mean(hm_ms)),
                           "classify": float(np.mean(cls_ms)), "exact_fp32": ex_ms, "redo_fp64": float(np.mean(redo_ms)),
                           "library_total": float(np.mean(total_ms)),

@@ -205,6 +205,44 @@ dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double *nodes, int32_t
                          const double *face_nodes, const double *pose, double tol, int8_t *flags_out,
                          double *dist_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * After the cut: several cutting surfaces, artificial-boundary faces, and the
+ * unblank step of a moving grid (Sec. 4.2, final paragraphs; Algorithm
+ * "Artificial Boundary unblank procedure", Sec. 3).  One cut removes its
+ * DC_HOLE elements, and for a solid wall (DC_WALL) also its DC_FRINGE
+ * elements; an overset boundary (DC_OVERSET) keeps the elements it passes
+ * through.  iblank arrays are int8: 1 kept, 0 removed.  All arrays are device
+ * pointers; the calls allocate nothing, run on `stream` (NULL: the legacy
+ * default stream) and return after it has finished; counts are returned
+ * through host pointers.  Calls are serialised by a lock in the library.
+ * Errors: DC_EINVAL for NULL pointers, n_elem < 1 or an unknown kind,
+ * DC_ECUDA if a CUDA call fails.
+ * ------------------------------------------------------------------------- */
+enum { DC_WALL = 0, DC_OVERSET = 1 };
+
+/* iblank_out[e] = 0 if any of the n_cuts (1..8) cuts removes element e, else 1.
+ * flags: host array of n_cuts device pointers to int8 flag arrays [n_elem]
+ * (the output of dc_cut); kinds: host array of n_cuts DC_WALL / DC_OVERSET. */
+dc_status dc_blank_union(int32_t n_cuts, const int8_t* const *flags, const int32_t *kinds, int64_t n_elem,
+                         int8_t *iblank_out, void *stream);
+
+/* Artificial-boundary faces: ab_mask[e] has bit j (faces 0..5: xi = -1, +1,
+ * eta = -1, +1, zeta = -1, +1) set when element e is kept and its neighbour
+ * across face j is removed.  neighbours: [n_elem][6] int64 element indices,
+ * -1 where a face has no neighbour.  *n_ab receives the number of such faces. */
+dc_status dc_ab_faces(int64_t n_elem, const int8_t *iblank, const int64_t *neighbours, uint8_t *ab_mask,
+                      int64_t *n_ab, void *stream);
+
+/* The unblank step for one cut kind: flags_t and flags_tp are the cuts at the
+ * current time and at t + dt; iblank_prev the blanking of the previous step.
+ * Wall: removed now if removed by either cut; overset: if removed by both.
+ * iblank_out receives the new blanking, unblank_out[e] = 1 for the elements
+ * removed before and kept now (to be filled by interpolation), *n_unblank
+ * their number. */
+dc_status dc_unblank(int32_t kind, int64_t n_elem, const int8_t *iblank_prev, const int8_t *flags_t,
+                     const int8_t *flags_tp, int8_t *iblank_out, uint8_t *unblank_out, int64_t *n_unblank,
+                     void *stream);
+
 /* Library version string. */
 const char *dc_version(void);
 

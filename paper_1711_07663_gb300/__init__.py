@@ -22,6 +22,7 @@ __all__ = [
     "DC_HOLE", "DC_FIELD", "DC_FRINGE", "DC_FP64", "DC_FP32_RECHECK", "DirectCutError", "load", "lib_path",
     "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
     "dc_last_error", "dc_version", "dc_cut_noalloc", "Context", "EXPORTED",
+    "DC_WALL", "DC_OVERSET", "dc_blank_union", "dc_ab_faces", "dc_unblank", "structured_neighbours",
 ]
 
 DC_OK, DC_PENDING = 0, 1
@@ -30,7 +31,9 @@ DC_HOLE, DC_FIELD, DC_FRINGE = 0, 1, -1
 DC_FP64, DC_FP32_RECHECK = 0, 1
 
 EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
-            "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc")
+            "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc", "dc_blank_union", "dc_ab_faces",
+            "dc_unblank")
+DC_WALL, DC_OVERSET = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -112,6 +115,12 @@ def load(build_if_missing: bool = False):
         L.dc_version.restype = ctypes.c_char_p
         L.dc_cut_noalloc.argtypes = [i32, i64, P, i32, i64, P, P, ctypes.c_double, P, P, P]
         L.dc_cut_noalloc.restype = i32
+        L.dc_blank_union.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(i32), i64, P, P]
+        L.dc_blank_union.restype = i32
+        L.dc_ab_faces.argtypes = [i64, P, P, P, ctypes.POINTER(i64), P]
+        L.dc_ab_faces.restype = i32
+        L.dc_unblank.argtypes = [i32, i64, P, P, P, P, P, ctypes.POINTER(i64), P]
+        L.dc_unblank.restype = i32
         _lib = L
         return L
 
@@ -136,7 +145,7 @@ def _addr(x, dtype):
         return None, False, None
     if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
         import torch
-        want = {np.float64: torch.float64, np.int8: torch.int8}[dtype]
+        want = {np.float64: torch.float64, np.int8: torch.int8, np.uint8: torch.uint8, np.int64: torch.int64}[dtype]
         if x.dtype != want or not x.is_contiguous():
             raise TypeError(f"tensor must be contiguous {want}")
         return x.data_ptr(), bool(x.is_cuda), x
@@ -243,6 +252,62 @@ def dc_cut_noalloc(p, nodes, q, faces, flags_out, dist_out=None, pose=None, tol=
     _check(load().dc_cut_noalloc(int(p), int(nk.shape[0]), np_, int(q), int(fk.shape[0]), fp,
                                  None if pk is None else pk.ctypes.data, float(tol), op, dp,
                                  None if stream is None else int(stream)))
+
+
+def _dev(x, dtype, what):
+    p, dev, k = _addr(x, dtype)
+    if not dev:
+        raise ValueError(f"{what} must be a device tensor")
+    return p, k
+
+
+def dc_blank_union(flags, kinds, iblank_out, stream=None):
+    """iblank (1 kept, 0 removed) of several cuts: see dc_blank_union in the header."""
+    ptrs = [_dev(f, np.int8, "flags")[0] for f in flags]
+    ob, ok = _dev(iblank_out, np.int8, "iblank_out")
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    kk = (ctypes.c_int32 * len(kinds))(*[int(k) for k in kinds])
+    _check(load().dc_blank_union(len(ptrs), arr, kk, int(ok.shape[0]), ob, None if stream is None else int(stream)))
+
+
+def dc_ab_faces(iblank, neighbours, ab_mask, stream=None) -> int:
+    """Artificial-boundary face masks; returns the number of such faces."""
+    ib, ik = _dev(iblank, np.int8, "iblank")
+    nb, _ = _dev(neighbours, np.int64, "neighbours")
+    mb, _ = _dev(ab_mask, np.uint8, "ab_mask")
+    n = ctypes.c_int64(0)
+    _check(load().dc_ab_faces(int(ik.shape[0]), ib, nb, mb, ctypes.byref(n), None if stream is None else int(stream)))
+    return n.value
+
+
+def dc_unblank(kind, iblank_prev, flags_t, flags_tp, iblank_out, unblank_out, stream=None) -> int:
+    """The unblank step for one cut kind; returns the number of elements to unblank."""
+    pp, pk = _dev(iblank_prev, np.int8, "iblank_prev")
+    tp_, _ = _dev(flags_t, np.int8, "flags_t")
+    tq, _ = _dev(flags_tp, np.int8, "flags_tp")
+    ob, _ = _dev(iblank_out, np.int8, "iblank_out")
+    ub, _ = _dev(unblank_out, np.uint8, "unblank_out")
+    n = ctypes.c_int64(0)
+    _check(load().dc_unblank(int(kind), int(pk.shape[0]), pp, tp_, tq, ob, ub, ctypes.byref(n),
+                             None if stream is None else int(stream)))
+    return n.value
+
+
+def structured_neighbours(nx, ny, nz) -> np.ndarray:
+    """Face neighbours [n][6] int64 of the hexes of an nx*ny*nz block numbered
+    ex + nx*(ey + ny*ez), faces xi-, xi+, eta-, eta+, zeta-, zeta+; -1 on the
+    block boundary (the input dc_ab_faces takes for a structured grid)."""
+    ez, ey, ex = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    e = (ex + nx * (ey + ny * ez)).reshape(-1).astype(np.int64)
+    ex, ey, ez = ex.reshape(-1), ey.reshape(-1), ez.reshape(-1)
+    out = np.full((e.size, 6), -1, dtype=np.int64)
+    out[:, 0] = np.where(ex > 0, e - 1, -1)
+    out[:, 1] = np.where(ex < nx - 1, e + 1, -1)
+    out[:, 2] = np.where(ey > 0, e - nx, -1)
+    out[:, 3] = np.where(ey < ny - 1, e + nx, -1)
+    out[:, 4] = np.where(ez > 0, e - nx * ny, -1)
+    out[:, 5] = np.where(ez < nz - 1, e + nx * ny, -1)
+    return out
 
 
 def dc_destroy(ctx) -> None:

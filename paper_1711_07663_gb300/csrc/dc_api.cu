@@ -21,6 +21,7 @@
 
 #include "../../include/directcut.h"
 #include "dc_near.cuh"
+#include "dc_overset.cuh"
 
 using namespace dc;
 
@@ -1141,3 +1142,96 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   if (h.err & (ERR_ROUNDS | ERR_RECHECK)) return fail(DC_EINTERNAL, "exact test capacity exceeded (error bits 0x%x)", h.err);
   return DC_OK;
 }
+
+// ------------------------------------------------------------------ after the cut
+// Union of cuts, artificial-boundary faces and the unblank step (Sec. 4.2
+// final paragraphs; Algorithm "Artificial Boundary unblank procedure").  The
+// element-parallel kernels are in dc_overset.cuh; their counts come back
+// through a small library-owned device array, so these calls allocate nothing.
+namespace {
+
+static __device__ unsigned long long g_ov_count[64];  // one counter per device ordinal
+std::mutex g_ov_mu;
+
+dc_status ov_counter(unsigned long long** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(DC_EINVAL, "device ordinal %d beyond 63", dev);
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_ov_count));
+  *out = static_cast<unsigned long long*>(p) + dev;
+  return DC_OK;
+}
+
+unsigned ov_grid(long long n) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+}
+
+}  // namespace
+
+extern "C" {
+
+dc_status dc_blank_union(int32_t n_cuts, const int8_t* const* flags, const int32_t* kinds, int64_t n_elem,
+                         int8_t* iblank_out, void* stream) {
+  g_err.clear();
+  if (n_cuts < 1 || n_cuts > OV_MAX_CUTS) return fail(DC_EINVAL, "n_cuts must be 1..%d", OV_MAX_CUTS);
+  if (!flags || !kinds || !iblank_out || n_elem < 1) return fail(DC_EINVAL, "NULL argument or n_elem < 1");
+  CutSet cs{};
+  cs.n = n_cuts;
+  for (int k = 0; k < n_cuts; ++k) {
+    if (!flags[k]) return fail(DC_EINVAL, "flags[%d] is NULL", k);
+    if (kinds[k] != DC_WALL && kinds[k] != DC_OVERSET) return fail(DC_EINVAL, "kinds[%d] is not DC_WALL or DC_OVERSET", k);
+    cs.flags[k] = flags[k];
+    cs.kind[k] = kinds[k] == DC_WALL ? OV_WALL : OV_OVERSET;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_blank_union<<<ov_grid(n_elem), 256, 0, st>>>(cs, (long long)n_elem, iblank_out);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return DC_OK;
+}
+
+dc_status dc_ab_faces(int64_t n_elem, const int8_t* iblank, const int64_t* neighbours, uint8_t* ab_mask,
+                      int64_t* n_ab, void* stream) {
+  g_err.clear();
+  if (!iblank || !neighbours || !ab_mask || n_elem < 1) return fail(DC_EINVAL, "NULL argument or n_elem < 1");
+  std::lock_guard<std::mutex> lk(g_ov_mu);
+  unsigned long long* cnt = nullptr;
+  dc_status rc = ov_counter(&cnt);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  k_ab_faces<<<ov_grid(n_elem), 256, 0, st>>>((long long)n_elem, iblank, reinterpret_cast<const long long*>(neighbours),
+                                               ab_mask, cnt);
+  CK(cudaGetLastError());
+  unsigned long long h = 0;
+  CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (n_ab) *n_ab = (int64_t)h;
+  return DC_OK;
+}
+
+dc_status dc_unblank(int32_t kind, int64_t n_elem, const int8_t* iblank_prev, const int8_t* flags_t,
+                     const int8_t* flags_tp, int8_t* iblank_out, uint8_t* unblank_out, int64_t* n_unblank,
+                     void* stream) {
+  g_err.clear();
+  if (kind != DC_WALL && kind != DC_OVERSET) return fail(DC_EINVAL, "kind is not DC_WALL or DC_OVERSET");
+  if (!iblank_prev || !flags_t || !flags_tp || !iblank_out || !unblank_out || n_elem < 1)
+    return fail(DC_EINVAL, "NULL argument or n_elem < 1");
+  std::lock_guard<std::mutex> lk(g_ov_mu);
+  unsigned long long* cnt = nullptr;
+  dc_status rc = ov_counter(&cnt);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  k_unblank<<<ov_grid(n_elem), 256, 0, st>>>(kind == DC_WALL ? OV_WALL : OV_OVERSET, (long long)n_elem, iblank_prev,
+                                              flags_t, flags_tp, iblank_out, unblank_out, cnt);
+  CK(cudaGetLastError());
+  unsigned long long h = 0;
+  CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (n_unblank) *n_unblank = (int64_t)h;
+  return DC_OK;
+}
+
+}  // extern "C"

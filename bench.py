@@ -361,7 +361,7 @@ def run_ours(args, world, rank, local):
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          # dram__bytes_read.sum + dram__bytes_write.sum of one launch
                          # (profiles/k_near_main_scale64.md); null once the kernel changes
-                         "traffic": 9.37e6 if args.workload == "scale64" else None,
+                         "traffic": 9.45e6 if args.workload == "scale64" else None,
                          "flops_per_launch": flops, "pairs_per_launch": pairs, "pairs_full_test": pairs_full,
                          "flops_per_pair": {"separation": FLOPS_PER_SEP, "full": FLOPS_PER_PAIR},
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},

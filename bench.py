@@ -9,12 +9,16 @@ the surface (1.33 MB of face nodes, already on the device for `value`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One JSON line on stdout (rank 0).  value = N_E * N_F / cut time (element-face
-relations resolved per second, summed over ranks); `e2e` is the same metric
-through the C ABI with host buffers (face upload and flag download inside the
-timed region); `roofline` is the flags-only exact stage (k_near_main, the
-dominant kernel) against the FP32 ALU peak; `cpu_baseline` is the CPU oracle
-on a bounded sample of the workload.
+One JSON line on stdout (rank 0).  value = |S*| / cut time: the necessary
+element-face tests of one cut (the pairs any box-pruned exact method must
+evaluate, counted once by the oracle into tests/golden/necessary_pairs.json)
+resolved per second, summed over ranks; `effective_rate` = N_E * N_F / cut
+time.  `e2e` is the same metric through the C ABI with host buffers (face
+upload and flag download inside the timed region); `roofline` is the
+flags-only exact stage (k_near_main, the dominant kernel) against the FP32 ALU
+peak, with the algorithmic arithmetic of the exact test on S*; `cut_roofline`
+is the whole cut against max(bytes / HBM peak, flops / FP32 peak);
+`cpu_baseline` is the CPU oracle on a bounded sample of the workload.
 """
 from __future__ import annotations
 
@@ -43,6 +47,26 @@ FLOPS_PER_PAIR = 936.5
 FLOPS_PER_SEP = 139.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# resident-mesh bytes one cut must move: a FP32 box read and a flag written per
+# element, the FP32 frame of each element that needs the exact test (Q2: 27
+# nodes x 3 x 4 B), the FP64 face nodes (Q2: 9 x 3 x 8 B)
+BYTES_PER_ELEM = 25
+BYTES_PER_EXACT_ELEM = 324
+BYTES_PER_FACE = 216
+
+
+def necessary(workload):
+    """The oracle's count of the necessary pair set S* of a workload."""
+    with open(os.path.join(ROOT, "tests", "golden", "necessary_pairs.json")) as f:
+        return json.load(f)[workload]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
 
 
 def _scale64():
@@ -146,7 +170,8 @@ def barrier(world):
 # ----------------------------------------------------------------- CPU oracle leg
 def cpu_oracle_sample(case, seconds, seed=0):
     """Time the oracle (as it stands, all host cores) on random elements of the
-    workload until ~`seconds` of wall time; returns element-face tests/s."""
+    workload until ~`seconds` of wall time.  Returns (elements done, seconds,
+    threads); one whole cut takes seconds * N_E / done."""
     import oracle as O
     g = np.random.default_rng(seed)
     ncpu = os.cpu_count() or 1
@@ -158,30 +183,33 @@ def cpu_oracle_sample(case, seconds, seed=0):
         O.cut(case.p, case.nodes, case.q, case.faces, ids=ids)
         done += batch
     dt = time.perf_counter() - t0
-    return done * case.n_faces / dt, done, dt, ncpu
+    return done, dt, ncpu
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
     case = WORKLOADS[args.workload]()
+    s_star = necessary(args.workload)["s_star_pairs"]
     per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
-    vals = []
+    cut_s = []
     n_el = 0
     for _ in range(args.warmup if args.warmup < 2 else 1):
         cpu_oracle_sample(case, 0.5, seed=99)
     for k in range(args.steps):
-        v, done, dt, ncpu = cpu_oracle_sample(case, per_step, seed=k)
-        vals.append(v)
+        done, dt, ncpu = cpu_oracle_sample(case, per_step, seed=k)
+        cut_s.append(dt * case.n_elem / done)
         n_el += done
-    value = float(np.mean(vals))
-    ms = case.n_elem * case.n_faces / value * 1e3
-    sample = f"{n_el} random elements of the workload (of {case.n_elem}), {args.steps} steps of ~{per_step:.1f} s"
+    ms = float(np.mean(cut_s)) * 1e3
+    value = s_star / (ms * 1e-3)
+    sample = (f"{n_el} random elements of the workload (of {case.n_elem}), {args.steps} steps of ~{per_step:.1f} s; "
+              f"one cut = the sampled time scaled to all elements")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "n_elem": case.n_elem,
                                                          "n_faces": case.n_faces, "p": 2, "q": 2},
+        "effective_rate": case.n_elem * case.n_faces / (ms * 1e-3),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -257,7 +285,9 @@ def run_ours(args, world, rank, local):
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
     t_sum = max_over_ranks(float(step_ms.sum()), world)
     ms_per_step = t_sum / args.steps
-    value = world * NE * NF / (ms_per_step * 1e-3)
+    nec = necessary(args.workload)
+    S_STAR = nec["s_star_pairs"]
+    value = world * S_STAR / (ms_per_step * 1e-3)
 
     # plain single-instance FP64 path (same flags): "vs plain"
     plain_ms = None
@@ -320,27 +350,41 @@ def run_ours(args, world, rank, local):
         if k >= args.warmup:
             ub_ms.append(a.elapsed_time(b))
 
-    # roofline of the dominant kernel (the flags-only exact stage): ALU bound;
-    # every listed pair takes the separation test, the rest the full test
+    # roofline of the dominant kernel (the flags-only exact stage): ALU bound.
+    # Algorithmic arithmetic = the exact test on the necessary pair set S*:
+    # |S*| x n_Tc x n_T(F) triangle pairs x the flops of one triangle pair, with
+    # n_Tc = the 3 element faces at the nearest corner (lower count) or all 6
+    # (upper).  Executed arithmetic (what this kernel runs): every listed
+    # triangle pair takes the separation test, the undecided ones the full test.
     ex_ms = float(np.mean(exact_ms))
     pairs = float(np.mean(bulk))
     pairs_full = float(np.mean(full))
-    flops = pairs * FLOPS_PER_SEP + pairs_full * FLOPS_PER_PAIR
-    achieved = flops / (ex_ms * 1e-3) / 1e12
+    flops_exec = pairs * FLOPS_PER_SEP + pairs_full * FLOPS_PER_PAIR
+    flops_alg = S_STAR * nec["n_tc_lower"] * nec["n_tf"] * FLOPS_PER_PAIR
+    flops_alg_upper = S_STAR * nec["n_tc_upper"] * nec["n_tf"] * FLOPS_PER_PAIR
+    achieved = flops_alg / (ex_ms * 1e-3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # the whole cut: T* = max(bytes / HBM peak, flops / FP32 peak)
+    hbm = measured_peaks().get("hbm_gbs")
+    cut_bytes = NE * BYTES_PER_ELEM + nec["exact_test_elements"] * BYTES_PER_EXACT_ELEM + NF * BYTES_PER_FACE
+    t_bytes_us = cut_bytes / (hbm * 1e9) * 1e6 if hbm else None
+    t_flops_us = flops_alg / (peak * 1e12) * 1e6
+    t_star_us = max(t_flops_us, t_bytes_us or 0.0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, done, dt, ncpu = cpu_oracle_sample(case, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": ncpu, "kind": "oracle",
-               "sample": f"{done} random elements of the workload ({dt:.1f} s, all {ncpu} host threads)"}
+        done, dt, ncpu = cpu_oracle_sample(case, args.cpu_seconds)
+        cpu = {"value": S_STAR * done / NE / dt, "unit": UNIT, "cores": ncpu, "kind": "oracle",
+               "sample": f"{done} random elements of the workload ({dt:.1f} s, all {ncpu} host threads); "
+                         f"one cut = the sampled time scaled to all {NE} elements"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "effective_rate": world * NE * NF / (ms_per_step * 1e-3), "s_star_pairs": S_STAR,
             "config": {"workload": WORKLOAD if args.workload == "scale64" else args.workload, "n_elem": NE, "n_faces": NF, "p": 2, "q": 2,
                        "precision": "fp32 bulk + fp64 re-solve", "mesh": "resident",
                        "l2": "flushed (256 MB write) between timed steps",
@@ -354,7 +398,7 @@ def run_ours(args, world, rank, local):
                           "library_total": float(np.mean(total_ms)),
                           "note": "separate profiled context (events between phases)"},
             "candidates": int(np.mean(ncand)), "pairs_fp32": int(pairs), "pairs_fp64": int(np.mean(rech)),
-            "e2e": {"value": world * NE * NF / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+            "e2e": {"value": world * S_STAR / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                     "h2d_bytes_per_step": int(case.faces.nbytes), "d2h_bytes_per_step": int(NE), "same_flags": e2e_same},
             "gpu_launches": 8 * args.steps,
             "roofline": {"bound": "alu", "kernel": "k_near_main (flags-only exact stage)", "achieved": achieved,
@@ -362,9 +406,17 @@ def run_ours(args, world, rank, local):
                          # dram__bytes_read.sum + dram__bytes_write.sum of one launch
                          # (profiles/k_near_main_scale64.md); null once the kernel changes
                          "traffic": 9.45e6 if args.workload == "scale64" else None,
-                         "flops_per_launch": flops, "pairs_per_launch": pairs, "pairs_full_test": pairs_full,
+                         "flops_per_launch": flops_alg, "flops_upper_count": flops_alg_upper,
+                         "units": f"|S*| = {S_STAR} element-face pairs x {nec['n_tc_lower']} x {nec['n_tf']} "
+                                  f"triangle pairs x {FLOPS_PER_PAIR} flops",
+                         "executed_flops": flops_exec, "executed_tflops": flops_exec / (ex_ms * 1e-3) / 1e12,
+                         "pairs_per_launch": pairs, "pairs_full_test": pairs_full,
                          "flops_per_pair": {"separation": FLOPS_PER_SEP, "full": FLOPS_PER_PAIR},
+                         "duration_ms": ex_ms,
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+            "cut_roofline": {"t_star_us": t_star_us, "t_flops_us": t_flops_us, "t_bytes_us": t_bytes_us,
+                             "bytes": cut_bytes, "hbm_gbs": hbm, "frac": t_star_us / (ms_per_step * 1e3),
+                             "bound": "alu" if t_flops_us >= (t_bytes_us or 0.0) else "hbm"},
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

@@ -97,6 +97,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--workload", default="scale64", choices=sorted(WORKLOADS),
                     help="scale64 is the benchmark; the others are small cases for profiling")
     return ap.parse_args()
@@ -240,6 +241,10 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     ctx = dc.Context([(case.p, nodes)], precision=dc.DC_FP32_RECHECK, device=local)
+    tuning, tune_trials = None, 0
+    if not args.no_autotune:
+        # the autotuner's sweep of launch shapes on this workload (untimed)
+        tuning, tune_trials = ctx.autotune([0], [dict(q=case.q, faces=faces, flags_out=flags)], repeats=3)
     for _ in range(args.warmup):
         ctx.cut(0, case.q, faces, flags, stream=stream.cuda_stream)
     torch.cuda.synchronize()
@@ -270,6 +275,8 @@ def run_ours(args, world, rank, local):
     # phases (outside the timed loop: the events cost time and split the
     # kernels' programmatic launch chain)
     with dc.Context([(case.p, nodes)], precision=dc.DC_FP32_RECHECK, profile=1, device=local) as pctx:
+        if tuning is not None:
+            pctx.set_tuning(**{k: v for k, v in tuning.items() if k != "ms"})
         for k in range(max(args.warmup, 3) + 20):
             flush.fill_(k & 0xff)
             pctx.cut(0, case.q, faces, flags, stream=stream.cuda_stream)
@@ -393,6 +400,7 @@ def run_ours(args, world, rank, local):
             "plain_fp64_ms": plain_ms, "speedup_vs_plain": (plain_ms / float(np.median(step_ms))) if plain_ms else None,
             "plain_same_flags": same_flags,
             "unblank_step_ms": float(np.median(ub_ms)),
+            "tuning": None if tuning is None else dict(tuning, trials=tune_trials),
             "phases_ms": {"surface_bins": float(np.mean(surf_ms)), "holemap": float(np.mean(hm_ms)),
                           "classify": float(np.mean(cls_ms)), "exact_fp32": ex_ms, "redo_fp64": float(np.mean(redo_ms)),
                           "library_total": float(np.mean(total_ms)),

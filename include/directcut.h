@@ -161,6 +161,47 @@ dc_status dc_poll(dc_ctx *ctx, uint64_t ticket, int64_t timeout_us);
 /* Counters and (profile=1) phase times of the last dc_cut / dc_cut_batch. */
 dc_status dc_get_stats(dc_ctx *ctx, dc_stats *out);
 
+/* Launch shapes of a context's cuts.  None of them changes a result: every
+ * setting gives the same flags and distances, only the time differs.
+ *   cubes_per_edge   hole-map cubes per mean element edge when holemap_cells is
+ *                    0 (automatic), 0.5..4; 1.8 by default.  Finer maps leave
+ *                    fewer candidate elements but cost more cubes per face.
+ *   bin_cubes        hole-map cubes per face-bin side, 2..16 (at least
+ *                    min(dc_config.bin_cubes, 2)); dc_config.bin_cubes by default.
+ *   warps_per_cta    warps per block of the flags-only exact stage: 4, 8 or 16
+ *                    (8 by default); lowered at launch to what the element and
+ *                    face orders' shared memory allows.
+ *   cands_per_warp   candidate elements a warp takes from the shared cursor at
+ *                    once: 1, 2, 4 or 8 (1 by default).
+ *   ms               dc_autotune: median time of the chosen setting; ignored
+ *                    by dc_set_tuning. */
+typedef struct {
+    float cubes_per_edge;
+    int32_t bin_cubes;
+    int32_t warps_per_cta;
+    int32_t cands_per_warp;
+    float ms;
+} dc_tuning;
+
+/* The context's current launch shapes. */
+dc_status dc_get_tuning(dc_ctx *ctx, dc_tuning *out);
+
+/* Set the launch shapes of later cuts; DC_EINVAL (nothing changed) for a value
+ * outside the ranges above. */
+dc_status dc_set_tuning(dc_ctx *ctx, const dc_tuning *t);
+
+/* Autotuner: run the batch (as dc_cut_batch) under every setting of the sweep
+ *   cubes_per_edge {1.2, 1.8, 2.7} (only when holemap_cells is 0)
+ *   x bin_cubes {2, 4, 8} x warps_per_cta {4, 8, 16} x cands_per_warp {1, 2, 4, 8},
+ * one untimed run then `repeats` (1..50) runs timed by CUDA events on the
+ * context's stream, keep the setting with the smallest median time, set it on
+ * the context and run the batch once more with it, so the outputs hold its
+ * result.  *best (may be NULL) receives the setting and its median time;
+ * *n_trials (may be NULL) the number of settings timed.  Synchronous; the
+ * requests must not set async.  On an error the previous setting stays. */
+dc_status dc_autotune(dc_ctx *ctx, int32_t n, const int32_t *meshes, const dc_request *reqs, int32_t repeats,
+                      dc_tuning *best, int32_t *n_trials);
+
 /* Drain in-flight work, then free everything the context owns. */
 void dc_destroy(dc_ctx *ctx);
 

@@ -23,6 +23,7 @@ __all__ = [
     "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
     "dc_last_error", "dc_version", "dc_cut_noalloc", "Context", "EXPORTED",
     "DC_WALL", "DC_OVERSET", "dc_blank_union", "dc_ab_faces", "dc_unblank", "structured_neighbours",
+    "dc_get_tuning", "dc_set_tuning", "dc_autotune",
 ]
 
 DC_OK, DC_PENDING = 0, 1
@@ -32,7 +33,7 @@ DC_FP64, DC_FP32_RECHECK = 0, 1
 
 EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
             "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc", "dc_blank_union", "dc_ab_faces",
-            "dc_unblank")
+            "dc_unblank", "dc_get_tuning", "dc_set_tuning", "dc_autotune")
 DC_WALL, DC_OVERSET = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -72,6 +73,11 @@ class dc_stats(ctypes.Structure):
                [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_redo",
                                                   "ms_total")] + \
                [(n, ctypes.c_int64) for n in ("near_tasks", "n_full_search", "near_pairs_full")]
+
+
+class dc_tuning(ctypes.Structure):
+    _fields_ = [("cubes_per_edge", ctypes.c_float), ("bin_cubes", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("cands_per_warp", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 _lib = None
@@ -121,6 +127,13 @@ def load(build_if_missing: bool = False):
         L.dc_ab_faces.restype = i32
         L.dc_unblank.argtypes = [i32, i64, P, P, P, P, P, ctypes.POINTER(i64), P]
         L.dc_unblank.restype = i32
+        L.dc_get_tuning.argtypes = [P, ctypes.POINTER(dc_tuning)]
+        L.dc_get_tuning.restype = i32
+        L.dc_set_tuning.argtypes = [P, ctypes.POINTER(dc_tuning)]
+        L.dc_set_tuning.restype = i32
+        L.dc_autotune.argtypes = [P, i32, ctypes.POINTER(i32), ctypes.POINTER(dc_request), i32,
+                                  ctypes.POINTER(dc_tuning), ctypes.POINTER(i32)]
+        L.dc_autotune.restype = i32
         _lib = L
         return L
 
@@ -315,6 +328,45 @@ def dc_destroy(ctx) -> None:
         load().dc_destroy(ctx)
 
 
+def _tuning_dict(t):
+    return {n: getattr(t, n) for n, _ in dc_tuning._fields_}
+
+
+def dc_get_tuning(ctx) -> dict:
+    t = dc_tuning()
+    _check(load().dc_get_tuning(ctx, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def dc_set_tuning(ctx, **kw):
+    """Change some launch shapes (keys of dc_tuning); the others stay."""
+    t = dc_tuning()
+    _check(load().dc_get_tuning(ctx, ctypes.byref(t)))
+    for k, v in kw.items():
+        if k not in dict(dc_tuning._fields_):
+            raise KeyError(k)
+        setattr(t, k, v)
+    _check(load().dc_set_tuning(ctx, ctypes.byref(t)))
+
+
+def dc_autotune(ctx, meshes, requests, repeats=3):
+    """Sweep the launch shapes on a batch (requests as for dc_cut_batch), keep
+    the fastest on the context; returns (setting dict with its median ms,
+    number of settings timed)."""
+    n = len(requests)
+    arr = (dc_request * n)()
+    keep = []
+    for i, rq in enumerate(requests):
+        r, k = _request(rq["q"], rq["faces"], rq["flags_out"], rq.get("dist_out"), rq.get("pose"))
+        arr[i] = r
+        keep.append(k)
+    ms = (ctypes.c_int32 * n)(*[int(m) for m in meshes])
+    best = dc_tuning()
+    trials = ctypes.c_int32(0)
+    _check(load().dc_autotune(ctx, n, ms, arr, int(repeats), ctypes.byref(best), ctypes.byref(trials)))
+    return _tuning_dict(best), trials.value
+
+
 class Context:
     """Owning wrapper: Context([(p, nodes), ...], precision=..., ...)."""
 
@@ -341,6 +393,15 @@ class Context:
 
     def stats(self):
         return dc_get_stats(self.handle)
+
+    def tuning(self):
+        return dc_get_tuning(self.handle)
+
+    def set_tuning(self, **kw):
+        dc_set_tuning(self.handle, **kw)
+
+    def autotune(self, meshes, requests, repeats=3):
+        return dc_autotune(self.handle, meshes, requests, repeats)
 
     def close(self):
         if self.handle:

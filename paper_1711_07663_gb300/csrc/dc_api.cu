@@ -165,11 +165,12 @@ struct LaunchParams {
   // flags-only form of the exact stage (k_near_*), when some instance
   // asks for flags only
   bool near = false;
+  int wpc = 8, cpw = 1;  // its warps per block and candidates per cursor step
   bool operator==(const LaunchParams& o) const {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
            pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
-           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near;
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && wpc == o.wpc && cpw == o.cpw;
   }
 };
 
@@ -236,6 +237,8 @@ struct dc_ctx {
   dc_stats last{};
   int pmax = 1;
   int smem_optin = 0;  // per-block opt-in shared memory limit of the device
+  int near_dyn_max = 0;  // dynamic shared memory k_near_main may take per block
+  dc_tuning tune{1.8f, 4, 8, 1, 0.f};  // launch shapes (dc_set_tuning, dc_autotune)
   bool use_graphs = true;  // replay captured launch sequences (DC_NO_GRAPHS=1 disables)
 };
 
@@ -259,6 +262,10 @@ int nbins_cap(int bin_cubes) {
   int b = (MAX_DIM + bin_cubes - 1) / bin_cubes;
   return b * b * b;
 }
+
+// the smallest bins a context's arenas are sized for: the configured size, or
+// 2 cubes when that is larger (so a tuned size of 2 still fits)
+int bin_floor(const dc_config& cfg) { return cfg.bin_cubes < 2 ? cfg.bin_cubes : 2; }
 
 size_t cube_bytes() { return (size_t)MAX_DIM * MAX_DIM * CUBE_PITCH; }
 
@@ -299,7 +306,7 @@ cudaError_t launch_rows(bool pdl, Inst* d_inst, const long long* foff, int n, lo
 // bytes of arena a batch needs
 size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
   size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
-  int nb = nbins_cap(c->cfg.bin_cubes);
+  int nb = nbins_cap(bin_floor(c->cfg));
   for (auto& r : v) {
     long long F = r.req->n_faces;
     int npf = (r.req->q + 1) * (r.req->q + 1);
@@ -441,11 +448,17 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     // flags-only form: one kernel settles every candidate (full searches and
     // their FP64 redo included)
     NearBufs nb{d_cnt + 11};
-    const size_t sm = (size_t)near_region(pmax, qmax) * WPB;
+    const size_t per = (size_t)near_region(pmax, qmax);
+    int wpc = std::min(P.wpc, NEAR_MAX_WARPS);
+    while (wpc > 1 && per * wpc > (size_t)c->near_dyn_max) wpc >>= 1;
+    if (per * wpc > (size_t)c->near_dyn_max)
+      return fail(DC_EINVAL, "orders p=%d q=%d need %zu bytes of shared memory per warp", pmax, qmax, per);
+    const size_t sm = per * wpc;
     int occn = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, TB, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, 32 * wpc, sm);
     occn = std::max(occn, 1);
-    CK(launch_k(true, k_near_main, dim3(c->n_sm * occn), dim3(TB), sm, st, d_inst, cl, nb, pmax, qmax, d_cnt + 4));
+    CK(launch_k(true, k_near_main, dim3(c->n_sm * occn), dim3(32 * wpc), sm, st, d_inst, cl, nb, pmax, qmax, P.cpw,
+                d_cnt + 4));
     if (prof) CK(record(s.ev[5], st, capturing));
   } else if (P.precision == DC_FP32_RECHECK) {
     int occ = 0;
@@ -523,7 +536,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return r; };
   Inst* d_inst = (Inst*)take(sizeof(Inst) * n);
   long long* d_off = (long long*)take(sizeof(long long) * 2 * (n + 1));
-  const int nb = nbins_cap(c->cfg.bin_cubes);
+  const int nb = nbins_cap(bin_floor(c->cfg));
   long long fo = 0, eo = 0;
   for (int i = 0; i < n; ++i) {
     const dc_request* r = v[i].req;
@@ -566,7 +579,8 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.tol_f = float_up(c->cfg.tol);
     in.holemap_cells = c->cfg.holemap_cells;
     in.h_elem = m.h_elem;
-    in.bin_cubes = c->cfg.bin_cubes;
+    in.cubes_per_edge = c->tune.cubes_per_edge;
+    in.bin_cubes = c->tune.bin_cubes;
     in.want_dist = r->dist_out ? 1 : 0;
     for (int a = 0; a < 3; ++a) { in.sbox_key[a] = ~0ULL; in.sbox_key[3 + a] = 0ULL; }
     s.h_off[i] = fo;
@@ -605,6 +619,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   lp.n = n; lp.nf_total = nf_total; lp.ne_total = ne_total; lp.max_tri = max_tri; lp.max_f = max_f;
   lp.pmax = pmax; lp.qmax = qmax; lp.precision = c->cfg.precision; lp.prof = c->cfg.profile != 0;
   lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt;
+  lp.wpc = c->tune.warps_per_cta; lp.cpw = c->tune.cands_per_warp;
   {
     bool flags_only = false;
     for (auto& r : v) flags_only |= r.req->dist_out == nullptr;
@@ -788,7 +803,9 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
         cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fd.sharedSizeBytes)) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
+    c->near_dyn_max = (int)(c->smem_optin - fnm.sharedSizeBytes);
   }
+  c->tune.bin_cubes = cfg.bin_cubes;
   c->slots.resize(cfg.max_inflight);
   for (auto& s : c->slots) {
     dc_status st = init_slot(s, cfg.profile);
@@ -884,6 +901,115 @@ dc_status dc_cut_batch(dc_ctx* c, int32_t n, const int32_t* meshes, const dc_req
   }
   CK(cudaSetDevice(c->cfg.device));
   return run_sync(c, v, false, (cudaStream_t)reqs[0].stream);
+}
+
+// ---------------------------------------------------------------- tuning
+
+static dc_status check_tuning(const dc_ctx* c, const dc_tuning& t) {
+  if (!(t.cubes_per_edge >= 0.5f && t.cubes_per_edge <= 4.0f))
+    return fail(DC_EINVAL, "cubes_per_edge outside 0.5..4");
+  if (t.bin_cubes < bin_floor(c->cfg) || t.bin_cubes > 16)
+    return fail(DC_EINVAL, "bin_cubes outside %d..16", bin_floor(c->cfg));
+  if (t.warps_per_cta != 4 && t.warps_per_cta != 8 && t.warps_per_cta != 16)
+    return fail(DC_EINVAL, "warps_per_cta must be 4, 8 or 16");
+  if (t.cands_per_warp != 1 && t.cands_per_warp != 2 && t.cands_per_warp != 4 && t.cands_per_warp != 8)
+    return fail(DC_EINVAL, "cands_per_warp must be 1, 2, 4 or 8");
+  return DC_OK;
+}
+
+dc_status dc_get_tuning(dc_ctx* c, dc_tuning* out) {
+  g_err.clear();
+  if (!c || !out) return fail(DC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->tune;
+  return DC_OK;
+}
+
+dc_status dc_set_tuning(dc_ctx* c, const dc_tuning* t) {
+  g_err.clear();
+  if (!c || !t) return fail(DC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(c->mu);
+  dc_status rc = check_tuning(c, *t);
+  if (rc) return rc;
+  c->tune = *t;
+  c->tune.ms = 0.f;
+  return DC_OK;
+}
+
+dc_status dc_autotune(dc_ctx* c, int32_t n, const int32_t* meshes, const dc_request* reqs, int32_t repeats,
+                      dc_tuning* best, int32_t* n_trials) {
+  g_err.clear();
+  if (!c) return fail(DC_EINVAL, "ctx is NULL");
+  if (n < 1 || !meshes || !reqs) return fail(DC_EINVAL, "empty batch");
+  if (repeats < 1 || repeats > 50) return fail(DC_EINVAL, "repeats outside 1..50");
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<InstReq> v;
+  v.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    dc_status rc = validate_req(c, meshes[i], &reqs[i]);
+    if (rc) return rc;
+    if (reqs[i].async) return fail(DC_EINVAL, "dc_autotune is synchronous; async must be 0");
+    v.push_back({meshes[i], &reqs[i]});
+  }
+  CK(cudaSetDevice(c->cfg.device));
+  Slot& s = c->slots[0];
+  const cudaStream_t st = reqs[0].stream ? (cudaStream_t)reqs[0].stream : s.stream;
+  const dc_tuning saved = c->tune;
+  std::vector<float> cpes;
+  if (c->cfg.holemap_cells == 0) cpes = {1.2f, 1.8f, 2.7f};
+  else cpes = {saved.cubes_per_edge};
+  std::vector<int> bins;
+  for (int b : {2, 4, 8})
+    if (b >= bin_floor(c->cfg)) bins.push_back(b);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(DC_ECUDA, "cudaEventCreate failed");
+  }
+  auto done = [&](dc_status rc) {
+    if (rc) c->tune = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  };
+  dc_tuning bt = saved;
+  float bms = INFINITY;
+  int trials = 0;
+  std::vector<float> t(repeats);
+  // launch shapes outermost: each graph of a shape is captured once and
+  // replayed for the hole-map settings (instance data, not graph keys)
+  for (int wpc : {4, 8, 16})
+    for (int cpw : {1, 2, 4, 8})
+      for (float cpe : cpes)
+        for (int bc : bins) {
+          c->tune = dc_tuning{cpe, bc, wpc, cpw, 0.f};
+          dc_status rc = run_sync(c, v, false, st);  // untimed
+          if (rc) return done(rc);
+          for (int r = 0; r < repeats; ++r) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return done(fail(DC_ECUDA, "cudaEventRecord failed"));
+            rc = enqueue(c, s, v, st, false);
+            if (rc) return done(rc);
+            if (cudaEventRecord(e1, st) != cudaSuccess) return done(fail(DC_ECUDA, "cudaEventRecord failed"));
+            rc = finish(c, s, v, st);
+            if (rc) return done(rc);
+            if (cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) return done(fail(DC_ECUDA, "cudaEventElapsedTime failed"));
+          }
+          std::vector<float> u = t;
+          std::nth_element(u.begin(), u.begin() + repeats / 2, u.end());
+          const float med = u[repeats / 2];
+          ++trials;
+          if (med < bms) {
+            bms = med;
+            bt = c->tune;
+          }
+        }
+  bt.ms = bms;
+  c->tune = bt;
+  dc_status rc = run_sync(c, v, false, st);  // the outputs, with the chosen setting
+  if (rc) return done(rc);
+  if (best) *best = bt;
+  if (n_trials) *n_trials = trials;
+  return done(DC_OK);
 }
 
 dc_status dc_get_stats(dc_ctx* c, dc_stats* out) {

@@ -71,6 +71,7 @@ struct Inst {
   float tol_f;             // tol rounded up to float
   int holemap_cells;        // 0: automatic, from h_elem
   float h_elem;             // mean longest box side of the grid's elements
+  float cubes_per_edge;     // automatic resolution: cubes per mean element edge
   int bin_cubes;
   int want_dist;
   // derived on the device

@@ -294,8 +294,13 @@ __host__ __device__ inline int near_region(int pmax, int qmax) {
   return a > b ? a : b;
 }
 
-__global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, CandList cl, NearBufs nb, int pmax,
-                                                      int qmax, unsigned long long* __restrict__ gcnt) {
+// at most 16 warps per block (4, 8 or 16 are launched; 128 registers per
+// thread either way)
+constexpr int NEAR_MAX_WARPS = 16;
+
+__global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
+    k_near_main(Inst* __restrict__ I, CandList cl, NearBufs nb, int pmax, int qmax, int cpw,
+                unsigned long long* __restrict__ gcnt) {
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned char s_et[MAX_P][MAX_NTE][3], s_ft[MAX_Q][MAX_NTF][3];
@@ -306,8 +311,8 @@ __global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, Cand
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const NearLayout Lo = near_layout(pmax, qmax);
   unsigned char* ws = smem + (size_t)wid * near_region(pmax, qmax);
-  __shared__ WarpCtx<float> s_cf[8];
-  __shared__ WarpCtx<double> s_cd[8];
+  __shared__ WarpCtx<float> s_cf[NEAR_MAX_WARPS];
+  __shared__ WarpCtx<double> s_cd[NEAR_MAX_WARPS];
   ExCounters fcnt = {0, 0, 0, 0, 0, 0, 0};
   unsigned long long n_fs = 0;
   // the full search of one candidate: FP32 with FP64 re-solves, then wholly
@@ -328,17 +333,21 @@ __global__ void __launch_bounds__(256, 2) k_near_main(Inst* __restrict__ I, Cand
   int* ci = reinterpret_cast<int*>(ws + Lo.ci);
   int* pq = reinterpret_cast<int*>(ws + Lo.pq);
   int2* ul = reinterpret_cast<int2*>(ws + Lo.ul);
-  const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
   const unsigned long long ncand = ucount(cl.count, cl.cap);
   unsigned long long n_fringe = 0, n_hole = 0, n_field = 0, n_faces = 0, n_pairs = 0, n_full = 0, n_re = 0;
-  (void)nwarps;
+  unsigned long long w = 0, wend = 0;
   while (true) {
-    // candidates are taken from a shared cursor: their costs differ widely
-    unsigned long long w = 0;
-    if (lane == 0) w = atomicAdd(&cl.count[1], 1ull);
-    w = __shfl_sync(FULL, w, 0);
-    if (w >= ncand) break;
-    const unsigned long long ent = cl.cand[w];
+    // candidates are taken from a shared cursor, cpw at a time: their costs
+    // differ widely
+    if (w >= wend) {
+      unsigned long long w0 = 0;
+      if (lane == 0) w0 = atomicAdd(&cl.count[1], (unsigned long long)cpw);
+      w0 = __shfl_sync(FULL, w0, 0);
+      if (w0 >= ncand) break;
+      w = w0;
+      wend = w0 + (unsigned long long)cpw < ncand ? w0 + (unsigned long long)cpw : ncand;
+    }
+    const unsigned long long ent = cl.cand[w++];
     const Inst& in = I[(int)(ent >> 40)];
     const long long e = (long long)(ent & ((1ull << 40) - 1ull));
     if (in.want_dist) {

@@ -41,12 +41,13 @@ __device__ void grid_from_box(Inst& in) {
     atomicOr(&in.err, (int)ERR_DEGENERATE);
     L = 1.0;
   }
-  // cubes on the longest side: as configured, or about 1.8 per element edge
-  // (a map much finer than the elements only multiplies the cubes each
-  // element and face covers; a coarser one widens the band of candidates)
+  // cubes on the longest side: as configured, or cubes_per_edge (1.8 unless
+  // tuned) per element edge (a map much finer than the elements only
+  // multiplies the cubes each element and face covers; a coarser one widens
+  // the band of candidates)
   int cells = in.holemap_cells;
   if (cells <= 0) {
-    const double a = in.h_elem > 0.f ? 1.8 * L / (double)in.h_elem : 64.0;
+    const double a = in.h_elem > 0.f ? (double)in.cubes_per_edge * L / (double)in.h_elem : 64.0;
     cells = (int)fmin(fmax(a + 0.5, 16.0), (double)MAX_CELLS);
   }
   const double ds = L / cells;

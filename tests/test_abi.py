@@ -55,13 +55,15 @@ def test_struct_layouts_match_header(tmp_path):
         "S(dc_request); F(dc_request,q); F(dc_request,n_faces); F(dc_request,face_nodes); F(dc_request,pose);\n"
         "F(dc_request,flags_out); F(dc_request,dist_out); F(dc_request,on_device); F(dc_request,async); F(dc_request,stream);\n"
         "S(dc_stats); F(dc_stats,holemap_rows_undecided); F(dc_stats,ms_surface); F(dc_stats,ms_total);\n"
+        "S(dc_tuning); F(dc_tuning,cubes_per_edge); F(dc_tuning,bin_cubes); F(dc_tuning,warps_per_cta);\n"
+        "F(dc_tuning,cands_per_warp); F(dc_tuning,ms);\n"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
     rename = {"async": "async_"}
     for cname, pyt in (("dc_mesh_desc", dc.dc_mesh_desc), ("dc_config", dc.dc_config), ("dc_request", dc.dc_request),
-                       ("dc_stats", dc.dc_stats)):
+                       ("dc_stats", dc.dc_stats), ("dc_tuning", dc.dc_tuning)):
         assert int(got[cname]) == ctypes.sizeof(pyt), cname
         for key, val in got.items():
             if key.startswith(cname + "."):

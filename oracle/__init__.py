@@ -66,6 +66,14 @@ def lib():
             L.orc_point_surface.argtypes = [P, i64, P, P]
             L.orc_cut.restype = i32
             L.orc_cut.argtypes = [i32, i64, P, i32, i64, P, P, d, i32, P, i64, P, P, P, P, i32]
+            L.orc_obb.restype = None
+            L.orc_obb.argtypes = [P, i32, P, P, P]
+            L.orc_approx_dist.restype = d
+            L.orc_approx_dist.argtypes = [P, P, P, P]
+            L.orc_pass1.restype = d
+            L.orc_pass1.argtypes = [i32, P, i32, P, d, ctypes.POINTER(i32), ctypes.POINTER(d)]
+            L.orc_heuristic.restype = i32
+            L.orc_heuristic.argtypes = [i32, i64, P, i32, i64, P, P, d, i32, i32, P, i64, P, P, P, P, i32]
             _lib = L
     return _lib
 
@@ -172,3 +180,52 @@ def cut(p, nodes, q, faces, pose=None, tol=1e-7, brute=False, ids=None, nthreads
     if rc != 0:
         raise ValueError("orc_cut rejected its arguments")
     return flags, dist, pflags, dict(zip(STAT_NAMES, (int(x) for x in stats)))
+
+
+# ----------------------------------------------------------------- the paper's truncating variant
+MARGIN_NAMES = ("key_gap", "corner_gap", "d1_gap", "zero_tie_key_gap", "d2_tol_gap", "side_cos")
+
+
+def obb(pts):
+    """OBB of points [n][3]: (R rows = axes, box [6] in those axes, centroid)."""
+    pts = _f64(pts)
+    R = np.zeros(9)
+    box = np.zeros(6)
+    cg = np.zeros(3)
+    lib().orc_obb(_ptr(pts), pts.shape[0], _ptr(R), _ptr(box), _ptr(cg))
+    return R.reshape(3, 3), box, cg
+
+
+def approx_dist(R, Be, ecg, Xf):
+    """Alg. cp0 key of a face (corner nodes Xf [4][3]) against an element OBB."""
+    R, Be, ecg, Xf = _f64(R), _f64(Be), _f64(ecg), _f64(Xf)
+    return lib().orc_approx_dist(_ptr(R), _ptr(Be), _ptr(ecg), _ptr(Xf))
+
+
+def pass1(p, enodes, q, fnodes, tol=1e-7):
+    """Alg. cp1 on one element-face pair: (D1, corner, corner gap)."""
+    enodes, fnodes = _f64(enodes), _f64(fnodes)
+    c = ctypes.c_int(0)
+    g = ctypes.c_double(0.0)
+    d1 = lib().orc_pass1(p, _ptr(enodes), q, _ptr(fnodes), float(tol), ctypes.byref(c), ctypes.byref(g))
+    return d1, c.value, g.value
+
+
+def heuristic(p, nodes, q, faces, pose=None, tol=1e-7, nf1=16, nf2=4, ids=None, nthreads=0):
+    """The paper's truncating variant: (flags int8, flagset uint8, dist f64,
+    margins [n][6]); flagset bit (flag + 1) marks every flag an exact tie at the
+    second truncation allows."""
+    nodes, faces = _f64(nodes), _f64(faces)
+    ids_arr = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+    nev = nodes.shape[0] if ids_arr is None else ids_arr.shape[0]
+    flags = np.zeros(nev, dtype=np.int8)
+    fset = np.zeros(nev, dtype=np.uint8)
+    dist = np.zeros(nev, dtype=np.float64)
+    margins = np.zeros((nev, 6), dtype=np.float64)
+    pose_arr = None if pose is None else _f64(np.asarray(pose).reshape(3, 4))
+    rc = lib().orc_heuristic(p, nodes.shape[0], _ptr(nodes), q, faces.shape[0], _ptr(faces), _ptr(pose_arr),
+                             float(tol), int(nf1), int(nf2), _ptr(ids_arr), nev, _ptr(flags), _ptr(fset), _ptr(dist),
+                             _ptr(margins), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_heuristic rejected its arguments")
+    return flags, fset, dist, margins

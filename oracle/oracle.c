@@ -34,6 +34,13 @@
  *             (Alg. bboxdix) and the search stops once that lower bound exceeds
  *             the best distance found (branch and bound; nothing is truncated).
  *
+ * The paper's truncating variant (orc_heuristic, end of file) is here too:
+ * OBB keys, the 16 nearest faces, pass 1 on corner triangles, the 4 nearest,
+ * pass 2 on the three element faces at the nearest corner.  Its steps are
+ * pinned one by one; the effect of the truncations on the result is parity
+ * unpinned (the paper gives no reference output for it), and is what the tests
+ * measure against the exact result above.
+ *
  * Compile with -ffp-contract=off so a*b+c is never fused: the pose transform
  * below must round exactly like the element-wise form it is written in.
  */
@@ -548,4 +555,366 @@ double orc_point_surface(const double *P, int64_t ntri, const double *tris, doub
     }
     if (winding) *winding = orc_winding(P, ntri, tris);
     return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* the paper's truncating variant (Sec. 4.2 and Alg. cp0, bboxdix, cp1, cp2)  */
+/* ------------------------------------------------------------------------ */
+/*
+ * The fast variant the paper runs on every filtered element E, with the
+ * truncations it describes.  Parity unpinned: whether its answer matches the
+ * exact one depends on the truncation (the paper says so for skewed elements);
+ * the steps themselves are pinned separately (OBB, keys, pass 1, pass 2).
+ *
+ *   0. OBB of E from its 8 corner nodes: centroid e_cg, axes = eigenvectors of
+ *      the corners' covariance (cyclic Jacobi), extents B_e = box of the
+ *      rotated corners.
+ *   1. Alg. cp0: for every face F, rotate its 4 corner nodes into the OBB axes,
+ *      B_f = their box, key = 0.01 |f_cg - e_cg| + boxDist(B_f, B_e), f_cg
+ *      the mean of F's corners.  Keep the nf1 (16) smallest keys (ties: lower
+ *      face id).
+ *   2. Alg. cp1: for each kept face, corner c of E nearest to f_cg (lowest
+ *      index on ties); the 3 faces of E at c, each its corner quad split into 2
+ *      triangles; F's corner quad split into 2 triangles; D1 = the smallest of
+ *      the 12 triangle distances, 0 when below tol.  Keep the nf2 (4) smallest
+ *      D1 (ties: the key order of step 1).
+ *   3. Alg. cp2: for each face kept there, the order-p triangles of the 3
+ *      faces of E at its corner c against F's 2q^2 triangles; a distance below
+ *      tol makes the element intersecting.
+ *   4. Smallest distance below tol: FRINGE.  Otherwise the side from the
+ *      minimal vector and the outward normal, over the triangle pairs at the
+ *      smallest distance (the same tie rule as the exact oracle: coincident
+ *      surface points average their normals, otherwise the largest |dot|).
+ *
+ * margins[6] per element, how far each decision was from going the other way:
+ *   [0] key gap between the nf1-th and (nf1+1)-th face (INF when all kept),
+ *   [1] smallest gap between the nearest and second-nearest corner over the
+ *       kept faces, [2] D1 gap at the nf2 boundary (INF when both are 0),
+ *   [3] key gap of the two boundary faces when both D1 are 0 (else INF),
+ *   [4] |D2min - tol|, [5] the deciding |cos| of the side rule (INF when
+ *   FRINGE).
+ * flagset per element: bit (flag + 1) for each flag reached by the selection
+ * in the paper's order and by every other selection an exact D1 tie at the
+ * nf2 boundary allows (faces sharing the nearest edge tie exactly, and which
+ * of them a computation keeps is then a matter of rounding).
+ */
+static void jacobi3(double A[3][3], double V[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        double scale = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+        if (off <= 1e-15 * scale || off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {       /* A <- A J (columns p, q) */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {       /* A <- J^T A (rows p, q) */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {       /* V <- V J */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+/* OBB of n points: axes R (rows, unit) and box of the rotated points */
+void orc_obb(const double *pts, int n, double *R, double *box, double *cg) {
+    vec c = {0, 0, 0};
+    for (int i = 0; i < n; ++i) c = vadd(c, mk(pts + 3 * i));
+    c = vscale(c, 1.0 / n);
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, V[3][3];
+    for (int i = 0; i < n; ++i) {
+        vec d = vsub(mk(pts + 3 * i), c);
+        double v[3] = {d.x, d.y, d.z};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[a][b] += v[a] * v[b] / n;
+    }
+    jacobi3(A, V);
+    for (int r = 0; r < 3; ++r)
+        for (int a = 0; a < 3; ++a) R[3 * r + a] = V[a][r];   /* row r = eigenvector r */
+    for (int a = 0; a < 3; ++a) { box[a] = INFINITY; box[3 + a] = -INFINITY; }
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < 3; ++r) {
+            double x = R[3 * r] * pts[3 * i] + R[3 * r + 1] * pts[3 * i + 1] + R[3 * r + 2] * pts[3 * i + 2];
+            if (x < box[r]) box[r] = x;
+            if (x > box[3 + r]) box[3 + r] = x;
+        }
+    if (cg) store(cg, c);
+}
+
+/* Alg. cp0: approximate distance of face corners Xf[4] to an element OBB */
+double orc_approx_dist(const double *R, const double *Be, const double *ecg, const double *Xf) {
+    double Bf[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    vec fcg = {0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+        fcg = vadd(fcg, mk(Xf + 3 * i));
+        for (int r = 0; r < 3; ++r) {
+            double x = R[3 * r] * Xf[3 * i] + R[3 * r + 1] * Xf[3 * i + 1] + R[3 * r + 2] * Xf[3 * i + 2];
+            if (x < Bf[r]) Bf[r] = x;
+            if (x > Bf[3 + r]) Bf[3 + r] = x;
+        }
+    }
+    fcg = vscale(fcg, 0.25);
+    return 0.01 * vnorm(vsub(fcg, mk(ecg))) + orc_box_dist(Bf, Be);
+}
+
+/* corner c (i + 2j + 4k) of an order-p element: node (i p, j p, k p) */
+static int corner_node(int p, int c) { return node_index(p, (c & 1) * p, ((c >> 1) & 1) * p, ((c >> 2) & 1) * p); }
+
+/* Alg. cp1: nearest corner to the face centroid, and the distance between the
+ * corner triangles of the 3 element faces at that corner and the face's 2
+ * corner triangles (0 below tol).  Returns D1; *corner, *gap (second-nearest
+ * corner distance minus nearest). */
+double orc_pass1(int p, const double *en, int q, const double *fn, double tol, int *corner, double *gap) {
+    const int npf = (q + 1) * (q + 1);
+    int fc[4] = {0, q, npf - 1, q * (q + 1)};             /* (0,0) (q,0) (q,q) (0,q) */
+    vec fcg = {0, 0, 0};
+    for (int i = 0; i < 4; ++i) fcg = vadd(fcg, mk(fn + 3 * fc[i]));
+    fcg = vscale(fcg, 0.25);
+    double best = INFINITY, second = INFINITY;
+    int c = 0;
+    for (int i = 0; i < 8; ++i) {
+        double d = vnorm(vsub(mk(en + 3 * corner_node(p, i)), fcg));
+        if (d < best) { second = best; best = d; c = i; }
+        else if (d < second) second = d;
+    }
+    *corner = c;
+    *gap = second - best;
+    double TF[2][9];
+    int tf[2][3] = {{0, 1, 2}, {0, 2, 3}};                 /* (00,10,11), (00,11,01) */
+    for (int h = 0; h < 2; ++h)
+        for (int v = 0; v < 3; ++v) memcpy(TF[h] + 3 * v, fn + 3 * fc[tf[h][v]], 3 * sizeof(double));
+    int fsel[3] = {c & 1, 2 + ((c >> 1) & 1), 4 + ((c >> 2) & 1)};
+    double D = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        int f = fsel[k];
+        int n00 = face_node(p, f, 0, 0), n10 = face_node(p, f, p, 0), n11 = face_node(p, f, p, p), n01 = face_node(p, f, 0, p);
+        int tri[2][3] = {{n00, n10, n11}, {n00, n11, n01}};
+        for (int h = 0; h < 2; ++h) {
+            double TC[9];
+            for (int v = 0; v < 3; ++v) memcpy(TC + 3 * v, en + 3 * tri[h][v], 3 * sizeof(double));
+            for (int j = 0; j < 2; ++j) {
+                double d = orc_tritri(TC, TF[j], NULL, NULL);
+                if (d < D) D = d;
+            }
+        }
+    }
+    return D < tol ? 0.0 : D;
+}
+
+typedef struct { double key, d1; int64_t f; int rank, corner; } hface_t;
+static int cmp_key(const void *x, const void *y) {
+    const hface_t *a = (const hface_t *)x, *b = (const hface_t *)y;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
+    return (a->f < b->f) ? -1 : (a->f > b->f);
+}
+static int cmp_d1(const void *x, const void *y) {
+    const hface_t *a = (const hface_t *)x, *b = (const hface_t *)y;
+    if (a->d1 < b->d1) return -1;
+    if (a->d1 > b->d1) return 1;
+    return a->rank - b->rank;
+}
+
+/* pass 2 (Alg. cp2) of one kept face, computed once per element and face:
+ * the smallest triangle distance, whether one fell below tol, and the pairs
+ * within the tie limit of that smallest distance */
+typedef struct { int done, hit, nt, cap; double best; tie_t *ties; } pass2_t;
+
+static void heur_pass2(int p, int q, const double *etris, const double *stris, const hface_t *h, double tol,
+                       pass2_t *r) {
+    const int ntf = 2 * q * q, tpf = 2 * p * p;
+    const int c = h->corner;
+    const int fsel[3] = {c & 1, 2 + ((c >> 1) & 1), 4 + ((c >> 2) & 1)};
+    r->best = INFINITY;
+    r->hit = 0;
+    r->nt = 0;
+    for (int s = 0; s < 3 && !r->hit; ++s)
+        for (int t = 0; t < tpf && !r->hit; ++t) {
+            const double *Te = etris + 9 * (fsel[s] * tpf + t);
+            for (int ts = 0; ts < ntf; ++ts) {
+                double ca[3], cb[3];
+                double d = orc_tritri(Te, stris + 9 * (h->f * ntf + ts), ca, cb);
+                if (d < tol) { r->best = d; r->hit = 1; break; }   /* the "return 0" of Alg. cp2 */
+                if (d <= tie_limit(r->best)) {
+                    if (r->nt == r->cap) { r->cap *= 2; r->ties = (tie_t *)realloc(r->ties, sizeof(tie_t) * r->cap); }
+                    r->ties[r->nt].d = d; r->ties[r->nt].ce = mk(ca); r->ties[r->nt].cs = mk(cb);
+                    r->ties[r->nt].ts = h->f * ntf + ts;
+                    ++r->nt;
+                    if (d < r->best) {
+                        r->best = d;
+                        int w = 0;
+                        for (int j = 0; j < r->nt; ++j)
+                            if (r->ties[j].d <= tie_limit(r->best)) r->ties[w++] = r->ties[j];
+                        r->nt = w;
+                    }
+                }
+            }
+        }
+    r->done = 1;
+}
+
+/* steps 3-4 for the kept faces sel[0..nsel): FRINGE when a distance falls
+ * below tol, else the side rule over the pairs at the smallest distance */
+static int8_t heur_decide(int p, int q, const double *en, const double *etris, const double *stris,
+                          const hface_t *hf, const int *sel, int nsel, pass2_t *p2, double tol, double scale,
+                          double *best_out, tie_t **ties, int *tcap, double *cosmag) {
+    (void)en;
+    double best = INFINITY;
+    int hit = 0;
+    for (int i = 0; i < nsel; ++i) {
+        pass2_t *r = &p2[sel[i]];
+        if (!r->done) heur_pass2(p, q, etris, stris, &hf[sel[i]], tol, r);
+        if (r->hit) hit = 1;
+        if (r->best < best) best = r->best;
+    }
+    *best_out = best;
+    *cosmag = INFINITY;
+    if (hit || best < tol) return ORC_FRINGE;
+    int nt = 0;
+    for (int i = 0; i < nsel; ++i) {
+        const pass2_t *r = &p2[sel[i]];
+        for (int j = 0; j < r->nt; ++j)
+            if (r->ties[j].d <= tie_limit(best)) {
+                if (nt == *tcap) { *tcap *= 2; *ties = (tie_t *)realloc(*ties, sizeof(tie_t) * (*tcap)); }
+                (*ties)[nt++] = r->ties[j];
+            }
+    }
+    double mag;
+    int s = paper_side(*ties, nt, stris, 1e-9 * scale, &mag);
+    *cosmag = mag;
+    return s > 0 ? ORC_FIELD : ORC_HOLE;
+}
+
+int orc_heuristic(int p, int64_t n_elem, const double *nodes, int q, int64_t n_faces, const double *faces,
+                  const double *pose, double tol, int nf1, int nf2, const int64_t *ids, int64_t n_ids, int8_t *flags,
+                  uint8_t *flagset, double *dist, double *margins, int nthreads) {
+    if (p < 1 || q < 1 || n_elem < 0 || n_faces < 1 || !nodes || !faces || nf1 < 1 || nf2 < 1 || nf2 > nf1 || nf1 > 64)
+        return -1;
+    const int npe = (p + 1) * (p + 1) * (p + 1), npf = (q + 1) * (q + 1);
+    const int nte = 12 * p * p, ntf = 2 * q * q, tpf = 2 * p * p;
+    const int64_t nts = n_faces * ntf;
+    const int64_t nev = ids ? n_ids : n_elem;
+    double *fx = (double *)malloc(sizeof(double) * 3 * npf * n_faces);
+    if (pose) orc_apply_pose(npf * n_faces, faces, pose, fx);
+    else memcpy(fx, faces, sizeof(double) * 3 * npf * n_faces);
+    double *stris = (double *)malloc(sizeof(double) * 9 * nts);
+    double *fcorn = (double *)malloc(sizeof(double) * 12 * n_faces);
+    const int fc[4] = {0, q, npf - 1, q * (q + 1)};
+    for (int64_t f = 0; f < n_faces; ++f) {
+        orc_face_tris(q, fx + 3 * npf * f, stris + 9 * ntf * f);
+        for (int i = 0; i < 4; ++i) memcpy(fcorn + 12 * f + 3 * i, fx + 3 * (npf * f + fc[i]), 3 * sizeof(double));
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        hface_t *hf = (hface_t *)malloc(sizeof(hface_t) * (size_t)n_faces);
+        double *etris = (double *)malloc(sizeof(double) * 9 * nte);
+        int tcap = 256;
+        tie_t *ties = (tie_t *)malloc(sizeof(tie_t) * tcap);
+        pass2_t p2[64];
+        for (int i = 0; i < 64; ++i) { p2[i].cap = 32; p2[i].ties = (tie_t *)malloc(sizeof(tie_t) * 32); }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < nev; ++k) {
+            int64_t e = ids ? ids[k] : k;
+            const double *en = nodes + 3 * npe * e;
+            double cpts[24], R[9], Be[6], ecg[3];
+            for (int c = 0; c < 8; ++c) memcpy(cpts + 3 * c, en + 3 * corner_node(p, c), 3 * sizeof(double));
+            orc_obb(cpts, 8, R, Be, ecg);
+            /* step 1 */
+            for (int64_t f = 0; f < n_faces; ++f) {
+                hf[f].key = orc_approx_dist(R, Be, ecg, fcorn + 12 * f);
+                hf[f].f = f;
+            }
+            qsort(hf, (size_t)n_faces, sizeof(hface_t), cmp_key);
+            const int n1 = n_faces < nf1 ? (int)n_faces : nf1;
+            double m[6] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+            if (n_faces > nf1) m[0] = hf[nf1].key - hf[nf1 - 1].key;
+            /* step 2 */
+            for (int i = 0; i < n1; ++i) {
+                double gap;
+                hf[i].rank = i;
+                hf[i].d1 = orc_pass1(p, en, q, fx + 3 * npf * hf[i].f, tol, &hf[i].corner, &gap);
+                if (gap < m[1]) m[1] = gap;
+            }
+            qsort(hf, (size_t)n1, sizeof(hface_t), cmp_d1);
+            const int n2 = n1 < nf2 ? n1 : nf2;
+            if (n1 > nf2) {
+                const hface_t *a = &hf[nf2 - 1], *b = &hf[nf2];
+                if (a->d1 == 0.0 && b->d1 == 0.0) {
+                    /* both zero: the key order of step 1 decided */
+                    m[3] = fabs(hf[nf2].key - hf[nf2 - 1].key);
+                    for (int i = 0; i < nf2; ++i)
+                        if (hf[i].d1 == 0.0) {
+                            for (int j = nf2; j < n1; ++j)
+                                if (hf[j].d1 == 0.0 && fabs(hf[j].key - hf[i].key) < m[3]) m[3] = fabs(hf[j].key - hf[i].key);
+                        }
+                } else {
+                    m[2] = b->d1 - a->d1;
+                }
+            }
+            /* steps 3-4 for the selection the paper's order gives, and for every
+             * other selection that an exact D1 tie at the nf2 boundary allows */
+            orc_elem_tris(p, en, etris);
+            double scale = 0.0;
+            for (int a = 0; a < 3; ++a) if (Be[3 + a] - Be[a] > scale) scale = Be[3 + a] - Be[a];
+            for (int i = 0; i < n1; ++i) p2[i].done = 0;
+            int sel[64], nsel = 0;
+            for (int i = 0; i < n2; ++i) sel[nsel++] = i;
+            double best;
+            int8_t fl = heur_decide(p, q, en, etris, stris, hf, sel, nsel, p2, tol, scale, &best, &ties, &tcap, &m[5]);
+            m[4] = fabs(best - tol);
+            unsigned fs = 1u << (fl + 1);
+            if (n1 > nf2 && hf[nf2 - 1].d1 > 0.0) {
+                const double v = hf[nf2 - 1].d1, lim = v * (1.0 + 1e-12) + 1e-15;
+                int lo = 0, hiT = 0;       /* faces below the tie band, faces in it */
+                int tied[16];
+                for (int i = 0; i < n1; ++i) {
+                    if (hf[i].d1 < v - (lim - v)) ++lo;
+                    else if (hf[i].d1 <= lim && hiT < 16) tied[hiT++] = i;
+                }
+                const int need = nf2 - lo;
+                if (hiT > need && need > 0 && hiT <= 12) {
+                    for (unsigned mask = 0; mask < (1u << hiT); ++mask) {
+                        if (__builtin_popcount(mask) != need) continue;
+                        nsel = 0;
+                        for (int i = 0; i < lo; ++i) sel[nsel++] = i;
+                        for (int t = 0; t < hiT; ++t) if (mask >> t & 1u) sel[nsel++] = tied[t];
+                        double b2, c2;
+                        int8_t f2 = heur_decide(p, q, en, etris, stris, hf, sel, nsel, p2, tol, scale, &b2, &ties, &tcap, &c2);
+                        fs |= 1u << (f2 + 1);
+                    }
+                } else if (hiT > need && need > 0) {
+                    fs = 7u;   /* too many tied faces to enumerate: any flag */
+                }
+            }
+            if (flags) flags[k] = fl;
+            if (flagset) flagset[k] = (uint8_t)fs;
+            if (dist) dist[k] = fl == ORC_HOLE ? -best : best;
+            if (margins) memcpy(margins + 6 * k, m, sizeof(m));
+        }
+        free(hf);
+        free(etris);
+        free(ties);
+        for (int i = 0; i < 64; ++i) free(p2[i].ties);
+    }
+    free(fx);
+    free(stris);
+    free(fcorn);
+    return 0;
 }

@@ -1,0 +1,168 @@
+"""Pins of the oracle's version of the paper's truncating variant (Sec. 4.2,
+Alg. cp0 / bboxdix / cp1 / cp2): the OBB against numpy's symmetric eigensolver,
+the approximate distance by hand and under rigid motion, pass 1 on boxes with
+known distances and nearest corners, and the whole variant against the exact
+oracle (never closer than the exact distance, never a false fringe, equal
+where faces are no smaller than the elements, missing fringe elements where
+many small faces crowd a large element, as the paper warns)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+
+def box_corners(lo, hi):
+    """8 corners in corner order c = i + 2j + 4k."""
+    return np.array([[(lo[0], hi[0])[i], (lo[1], hi[1])[j], (lo[2], hi[2])[k]]
+                     for k in (0, 1) for j in (0, 1) for i in (0, 1)], dtype=float)
+
+
+def rot(axis, ang):
+    return W.axis_rotation(axis, ang)
+
+
+def test_obb_axes_are_the_covariance_eigenvectors():
+    g = np.random.default_rng(1)
+    for _ in range(5):
+        Q = rot(g.normal(size=3), g.uniform(0, np.pi))
+        pts = box_corners((0, 0, 0), (1.0, 2.0, 3.5)) @ Q.T + g.normal(size=3)
+        R, box, cg = O.obb(pts)
+        C = np.cov(pts.T, bias=True)
+        w, V = np.linalg.eigh(C)
+        # every OBB axis is parallel to one eigenvector (distinct eigenvalues)
+        overlap = np.abs(R @ V)
+        assert np.allclose(np.sort(overlap.max(axis=1)), 1.0, atol=1e-9)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert np.allclose(cg, pts.mean(axis=0), atol=1e-12)
+        ext = np.sort(box[3:] - box[:3])
+        assert np.allclose(ext, [1.0, 2.0, 3.5], atol=1e-9)
+        # tight: every rotated point inside, each face touched
+        r = pts @ R.T
+        assert np.all(r >= box[:3] - 1e-12) and np.all(r <= box[3:] + 1e-12)
+        assert np.allclose(r.min(0), box[:3]) and np.allclose(r.max(0), box[3:])
+
+
+def test_approx_dist_by_hand():
+    # axis-aligned unit cube: covariance 0.25 I exactly, axes = identity
+    R, Be, ecg = O.obb(box_corners((0, 0, 0), (1, 1, 1)))
+    assert np.array_equal(R, np.eye(3))
+    Xf = np.array([[2, 0, 0.5], [3, 0, 0.5], [3, 1, 0.5], [2, 1, 0.5]], dtype=float)
+    # box gap 1 along x, centroid distance |(2.5,.5,.5) - (.5,.5,.5)| = 2
+    assert O.approx_dist(R, Be, ecg, Xf) == pytest.approx(1.0 + 0.01 * 2.0, abs=1e-15)
+    # overlapping boxes: only the centroid term
+    Xf2 = np.array([[0.5, 0.5, 0.5], [1.5, 0.5, 0.5], [1.5, 1.5, 0.5], [0.5, 1.5, 0.5]], dtype=float)
+    assert O.approx_dist(R, Be, ecg, Xf2) == pytest.approx(0.01 * np.sqrt(0.5), abs=1e-15)
+
+
+def test_approx_dist_is_invariant_under_rigid_motion():
+    g = np.random.default_rng(2)
+    el = box_corners((0, 0, 0), (1.0, 1.7, 2.6)) + g.uniform(-0.05, 0.05, size=(8, 3))
+    faces = [g.uniform(-3, 3, size=3) + g.uniform(-0.4, 0.4, size=(4, 3)) for _ in range(12)]
+    R, Be, ecg = O.obb(el)
+    base = [O.approx_dist(R, Be, ecg, f) for f in faces]
+    for _ in range(4):
+        Q = rot(g.normal(size=3), g.uniform(0, 2 * np.pi))
+        t = g.normal(size=3)
+        R2, Be2, ecg2 = O.obb(el @ Q.T + t)
+        moved = [O.approx_dist(R2, Be2, ecg2, f @ Q.T + t) for f in faces]
+        assert np.allclose(moved, base, rtol=1e-9, atol=1e-12)
+
+
+def hex_p1(lo, hi):
+    """Order-1 element nodes (tensor order, i fastest) of an axis-aligned box."""
+    return box_corners(lo, hi)
+
+
+def quad_q1(c00, c10, c11, c01):
+    """Order-1 face nodes (i fastest): (0,0) (1,0) (0,1) (1,1)."""
+    return np.array([c00, c10, c01, c11], dtype=float)
+
+
+def test_pass1_distance_and_corner():
+    en = hex_p1((0, 0, 0), (1, 1, 1))
+    # above the top face, centroid over corner (1,1,1)
+    fn = quad_q1((0.7, 0.6, 1.5), (1.1, 0.6, 1.5), (1.1, 1.0, 1.5), (0.7, 1.0, 1.5))
+    d1, c, gap = O.pass1(1, en, 1, fn)
+    assert c == 7 and d1 == pytest.approx(0.5, abs=1e-15) and gap > 0
+    # below the bottom face near corner (0,0,0)
+    fn = quad_q1((-0.3, -0.2, -0.25), (0.2, -0.2, -0.25), (0.2, 0.3, -0.25), (-0.3, 0.3, -0.25))
+    d1, c, _ = O.pass1(1, en, 1, fn)
+    assert c == 0 and d1 == pytest.approx(0.25, abs=1e-15)
+    # a face through the element: 0
+    fn = quad_q1((0.2, 0.2, 0.5), (1.8, 0.2, 0.5), (1.8, 0.8, 0.5), (0.2, 0.8, 0.5))
+    assert O.pass1(1, en, 1, fn)[0] == 0.0
+    # a gap below tol is reported as 0 (Alg. cp1)
+    fn = quad_q1((0.2, 0.2, 1 + 5e-8), (0.8, 0.2, 1 + 5e-8), (0.8, 0.8, 1 + 5e-8), (0.2, 0.8, 1 + 5e-8))
+    assert O.pass1(1, en, 1, fn)[0] == 0.0
+    # corner ties take the lowest corner index
+    fn = quad_q1((0.25, 0.25, 2), (0.75, 0.25, 2), (0.75, 0.75, 2), (0.25, 0.75, 2))
+    d1, c, gap = O.pass1(1, en, 1, fn)
+    assert c == 4 and gap == 0.0 and d1 == pytest.approx(1.0, abs=1e-15)
+
+
+def test_pass1_on_higher_orders_uses_the_corner_nodes_only():
+    # an order-2 element whose mid-face node bulges towards the face: pass 1
+    # sees only the corners (the linear part), so its distance ignores the bulge
+    en = W.hex_block((0, 0, 0), (1, 1, 1), p=2)[0].copy()
+    top_mid = 1 + 3 * (1 + 3 * 2)          # node (1,1,2)
+    en[top_mid, 2] = 1.3
+    fn = np.array([[x, y, 1.5] for y in (0.0, 0.5, 1.0) for x in (0.0, 0.5, 1.0)], dtype=float)
+    d1, _, _ = O.pass1(2, en, 2, fn)
+    assert d1 == pytest.approx(0.5, abs=1e-15)
+
+
+def test_pass1_is_an_upper_bound_of_the_linear_distance():
+    g = np.random.default_rng(4)
+    en = hex_p1((0, 0, 0), (1, 1, 1)) + g.uniform(-0.05, 0.05, size=(8, 3))
+    etris = O.elem_tris(1, en)
+    for _ in range(40):
+        ctr = g.uniform(-2.5, 2.5, size=3)
+        fn = ctr + g.uniform(-0.5, 0.5, size=(4, 3))
+        d1, c, _ = O.pass1(1, en, 1, fn)
+        ftris = O.face_tris(1, fn)
+        full = min(O.tritri(a, b)[0] for a in etris for b in ftris)
+        assert d1 >= full - 1e-15 or (d1 == 0.0 and full < 1e-7)
+        # the three element faces at the nearest corner
+        faces_at_c = [c & 1, 2 + ((c >> 1) & 1), 4 + ((c >> 2) & 1)]
+        sub = min(O.tritri(etris[2 * f + h], b)[0] for f in faces_at_c for h in (0, 1) for b in ftris)
+        assert d1 == (0.0 if sub < 1e-7 else sub)
+
+
+def test_variant_against_the_exact_oracle_on_the_plain_workload():
+    c = W.sphere_in_box(n=16, p=2, m=8, q=2, seed=1)
+    fh, fs, dh, mg = O.heuristic(c.p, c.nodes, c.q, c.faces)
+    fe, de, _, _ = O.cut(c.p, c.nodes, c.q, c.faces)
+    # faces about as large as the elements: the truncation loses nothing here
+    assert np.array_equal(fh, fe)
+    assert np.all(fs & (1 << (fh.astype(np.int16) + 1)).astype(np.uint8))
+    assert np.all(np.abs(dh) >= np.abs(de) * (1 - 1e-12) - 1e-15)
+
+
+@pytest.mark.parametrize("n,p,m,q,jit", [(6, 1, 32, 1, 0.05), (8, 2, 24, 2, 0.05)])
+def test_variant_misses_fringe_elements_among_many_small_faces(n, p, m, q, jit):
+    nodes = W.background(n, p, jitter=jit, seed=3)
+    faces = W.cubed_sphere(m, q, radius=1.0, centre=(0.03, -0.02, 0.05))
+    fh, fs, dh, _ = O.heuristic(p, nodes, q, faces)
+    fe, de, _, _ = O.cut(p, nodes, q, faces)
+    # it only ever searches a subset of the pairs: never closer, never a false
+    # fringe ...
+    assert np.all(np.abs(dh) >= np.abs(de) * (1 - 1e-12) - 1e-15)
+    assert not np.any((fh == O.FRINGE) & (fe != O.FRINGE))
+    # ... and with hundreds of faces per element it keeps the wrong 16 for some
+    # elements that the surface passes through (Fig. dc-filt-0)
+    miss = (fe == O.FRINGE) & (fh != O.FRINGE)
+    assert miss.sum() > 0
+    assert np.array_equal(fh != fe, miss)
+
+
+def test_no_truncation_and_one_face():
+    # a single large face under the element: every truncation keeps it, the
+    # nearest corner is on the bottom face, so the variant finds the exact
+    # distance and the side
+    nodes = W.hex_block((0, 0, 0), (1, 1, 1), p=2, n=(3, 3, 3))
+    face = np.array([[[x, y, -0.5] for y in (-3.0, 0.0, 3.0) for x in (-3.0, 0.0, 3.0)]], dtype=float)
+    fh, _, dh, _ = O.heuristic(2, nodes, 2, face)
+    fe, de, _, _ = O.cut(2, nodes, 2, face)
+    assert np.array_equal(fh, fe)
+    assert np.allclose(np.abs(dh), np.abs(de), rtol=1e-14, atol=1e-15)

@@ -72,8 +72,16 @@ enum { DC_HOLE = 0, DC_FIELD = 1, DC_FRINGE = -1 };
  * prepass may use single precision).  DC_FP32_RECHECK evaluates all candidate
  * pairs in FP32 with certified error bounds and re-solves, in FP64, only the
  * pairs whose FP32 lower bound lies within the bound of the best distance;
- * DC_FP64 evaluates every pair in FP64.  Both give the same flags. */
-enum { DC_FP64 = 0, DC_FP32_RECHECK = 1 };
+ * DC_FP64 evaluates every pair in FP64.  Both give the same flags.
+ *
+ * DC_HEURISTIC is the paper's own truncating variant instead of the exact
+ * test (Sec. 4.2, Alg. cp0-cp2): per candidate, the 16 faces with the smallest
+ * OBB-box key, the 4 with the smallest corner-triangle distance, and the
+ * element triangles of the three faces at the nearest corner.  Its flags can
+ * differ from the exact ones (a fringe element whose nearest faces fall
+ * outside the 16 or 4 is reported hole or field); each of its decisions is
+ * taken as in FP64.  dist_out holds its (upper-bound) distance. */
+enum { DC_FP64 = 0, DC_FP32_RECHECK = 1, DC_HEURISTIC = 2 };
 
 typedef struct {
     int32_t p;                /* element order, 1..4 */
@@ -84,7 +92,7 @@ typedef struct {
 
 typedef struct {
     int32_t device;           /* CUDA device ordinal */
-    int32_t precision;        /* DC_FP32_RECHECK (default) or DC_FP64 */
+    int32_t precision;        /* DC_FP32_RECHECK (default), DC_FP64 or DC_HEURISTIC */
     size_t mem_budget_bytes;  /* device bytes the context may hold; 0 = no limit */
     double tol;               /* fringe tolerance, absolute mesh units; 0 -> 1e-7 (Alg. cp1) */
     int32_t holemap_cells;    /* hole-map cubes along the longest surface side, 8..80;
@@ -131,6 +139,10 @@ typedef struct {
                                  (distances requested, or no node labelled by the hole map) */
     int64_t near_pairs_full;  /* flags-only requests: listed triangle pairs that plane
                                  separation could not settle (full FP32 test) */
+    int64_t heur_rescans;     /* DC_HEURISTIC: candidates whose FP32 key scan could not
+                                 certify the 16 nearest faces (rescanned in FP64) */
+    int64_t heur_resolves;    /* DC_HEURISTIC: faces whose pass-1 distance was re-solved
+                                 in FP64 to order or zero it */
 } dc_stats;
 
 /* Fill *cfg with the defaults listed above. */

@@ -19,7 +19,8 @@ import threading
 import numpy as np
 
 __all__ = [
-    "DC_HOLE", "DC_FIELD", "DC_FRINGE", "DC_FP64", "DC_FP32_RECHECK", "DirectCutError", "load", "lib_path",
+    "DC_HOLE", "DC_FIELD", "DC_FRINGE", "DC_FP64", "DC_FP32_RECHECK", "DC_HEURISTIC", "DirectCutError", "load",
+    "lib_path",
     "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
     "dc_last_error", "dc_version", "dc_cut_noalloc", "Context", "EXPORTED",
     "DC_WALL", "DC_OVERSET", "dc_blank_union", "dc_ab_faces", "dc_unblank", "structured_neighbours",
@@ -29,7 +30,7 @@ __all__ = [
 DC_OK, DC_PENDING = 0, 1
 DC_EINVAL, DC_ENOMEM, DC_ECUDA, DC_EBUSY, DC_ETIMEDOUT, DC_ENOTFOUND, DC_ECANCELED, DC_EINTERNAL = range(-1, -9, -1)
 DC_HOLE, DC_FIELD, DC_FRINGE = 0, 1, -1
-DC_FP64, DC_FP32_RECHECK = 0, 1
+DC_FP64, DC_FP32_RECHECK, DC_HEURISTIC = 0, 1, 2
 
 EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
             "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc", "dc_blank_union", "dc_ab_faces",
@@ -72,7 +73,8 @@ class dc_stats(ctypes.Structure):
                                              "holemap_rows_undecided")] + \
                [(n, ctypes.c_float) for n in ("ms_surface", "ms_holemap", "ms_classify", "ms_exact", "ms_redo",
                                                   "ms_total")] + \
-               [(n, ctypes.c_int64) for n in ("near_tasks", "n_full_search", "near_pairs_full")]
+               [(n, ctypes.c_int64) for n in ("near_tasks", "n_full_search", "near_pairs_full", "heur_rescans",
+                                              "heur_resolves")]
 
 
 class dc_tuning(ctypes.Structure):

@@ -22,6 +22,7 @@
 #include "../../include/directcut.h"
 #include "dc_near.cuh"
 #include "dc_overset.cuh"
+#include "dc_heur.cuh"
 
 using namespace dc;
 
@@ -166,11 +167,13 @@ struct LaunchParams {
   // asks for flags only
   bool near = false;
   int wpc = 8, cpw = 1;  // its warps per block and candidates per cursor step
+  int* hsel = nullptr;   // truncating variant: kept faces per candidate
   bool operator==(const LaunchParams& o) const {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
            pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
-           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && wpc == o.wpc && cpw == o.cpw;
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && wpc == o.wpc && cpw == o.cpw &&
+           hsel == o.hsel;
   }
 };
 
@@ -221,7 +224,8 @@ struct Slot {
 constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters,
                           // [11] near faces tested, [12] holes decided by the hole map,
                           // [14] near full searches, [16] near pairs given the
-                          // full FP32 test
+                          // full FP32 test, [17] truncating variant: FP64 key
+                          // rescans, [18] FP64 pass-1 re-solves
 
 }  // namespace
 
@@ -311,11 +315,13 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
     long long F = r.req->n_faces;
     int npf = (r.req->q + 1) * (r.req->q + 1);
     if (!r.req->on_device) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
+    if (c->cfg.precision == DC_HEURISTIC) s += al256(sizeof(float) * 16 * F);
     s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(float) * F * 6) +
          al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) +
          run_bytes();
   }
   s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
+  if (c->cfg.precision == DC_HEURISTIC) s += al256(sizeof(int) * HEUR_SEL * ne_total);  // kept faces
   s += al256(sizeof(unsigned long long) * NCNT);
   s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
   return s;
@@ -444,7 +450,23 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
   if ((long long)Ld.total * WPB > c->smem_optin)
     return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", pmax, qmax, Ld.total * WPB);
   CandList none{redo, 0, d_cnt + 2};
-  if (P.precision == DC_FP32_RECHECK && P.near) {
+  if (P.precision == DC_HEURISTIC) {
+    // the paper's truncating variant: kept faces per candidate, then pass 2
+    // (FP32 with FP64 re-solves; FP64 for the elements whose list overflowed)
+    CK(launch_k(true, k_heur_faces, dim3((unsigned)((P.max_f + TB - 1) / TB), n), dim3(TB), 0, st, d_inst));
+    int occs = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs, k_heur_select, TB, 0);
+    occs = std::max(occs, 1);
+    CK(launch_k(true, k_heur_select, dim3(c->n_sm * occs), dim3(TB), 0, st, d_inst, cl, P.hsel, d_cnt + 17));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_heur_final<float>, TB, (size_t)Lf.total * WPB);
+    occ = std::max(occ, 1);
+    CK(launch_k(true, k_heur_final<float>, dim3(c->n_sm * occ), dim3(TB), (size_t)Lf.total * WPB, st, d_inst, cl, rl,
+                (const int*)P.hsel, 0, pmax, qmax, d_cnt + 4));
+    if (prof) CK(record(s.ev[5], st, capturing));
+    CK(launch_k(true, k_heur_final<double>, dim3(std::min(c->n_sm, 16)), dim3(TB), (size_t)Ld.total * WPB, st, d_inst,
+                cl, rl, (const int*)P.hsel, 1, pmax, qmax, d_cnt + 4));
+  } else if (P.precision == DC_FP32_RECHECK && P.near) {
     // flags-only form: one kernel settles every candidate (full searches and
     // their FP64 redo included)
     NearBufs nb{d_cnt + 11};
@@ -563,6 +585,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.has_pose = r->pose ? 1 : 0;
     if (r->pose) memcpy(in.pose, r->pose, sizeof(double) * 12);
     in.surf = (double*)take(sizeof(double) * F * npf * 3);
+    if (c->cfg.precision == DC_HEURISTIC) in.hface = (float*)take(sizeof(float) * 16 * F);
     in.fbox = (float*)take(sizeof(float) * F * 6);
     in.fbin = (int*)take(sizeof(int) * F);
     in.bin_faces = (int*)take(sizeof(int) * F);
@@ -592,6 +615,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   s.h_off[2 * n + 1] = eo;
   unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
+  int* hsel = c->cfg.precision == DC_HEURISTIC ? (int*)take(sizeof(int) * HEUR_SEL * ne_total) : nullptr;
   unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
   int8_t* oflags = (int8_t*)take(ne_total);
   double* odist = (double*)take(sizeof(double) * ne_total);
@@ -618,7 +642,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   LaunchParams lp;
   lp.n = n; lp.nf_total = nf_total; lp.ne_total = ne_total; lp.max_tri = max_tri; lp.max_f = max_f;
   lp.pmax = pmax; lp.qmax = qmax; lp.precision = c->cfg.precision; lp.prof = c->cfg.profile != 0;
-  lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt;
+  lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt; lp.hsel = hsel;
   lp.wpc = c->tune.warps_per_cta; lp.cpw = c->tune.cands_per_warp;
   {
     bool flags_only = false;
@@ -667,6 +691,8 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
   S.near_tasks = s.near ? (int64_t)s.h_cnt[11] : 0;
   S.n_full_search = s.near ? (int64_t)s.h_cnt[14] : (int64_t)s.h_cnt[0];
   S.near_pairs_full = s.near ? (int64_t)s.h_cnt[16] : 0;
+  S.heur_rescans = (int64_t)s.h_cnt[17];
+  S.heur_resolves = (int64_t)s.h_cnt[18];
   if (c->cfg.profile) {
     cudaEventElapsedTime(&S.ms_surface, s.ev[0], s.ev[1]);
     cudaEventElapsedTime(&S.ms_holemap, s.ev[1], s.ev[2]);
@@ -763,7 +789,8 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     return fail(DC_EINVAL, "holemap_cells outside 8..%d (or 0: automatic)", MAX_CELLS);
   if (cfg.bin_cubes < 1 || cfg.bin_cubes > 16) return fail(DC_EINVAL, "bin_cubes outside 1..16");
   if (cfg.max_inflight < 1 || cfg.max_inflight > 64) return fail(DC_EINVAL, "max_inflight outside 1..64");
-  if (cfg.precision != DC_FP64 && cfg.precision != DC_FP32_RECHECK) return fail(DC_EINVAL, "unknown precision %d", cfg.precision);
+  if (cfg.precision != DC_FP64 && cfg.precision != DC_FP32_RECHECK && cfg.precision != DC_HEURISTIC)
+    return fail(DC_EINVAL, "unknown precision %d", cfg.precision);
   if (n_meshes < 1 || !meshes) return fail(DC_EINVAL, "at least one mesh is required");
   for (int i = 0; i < n_meshes; ++i) {
     const dc_mesh_desc& m = meshes[i];
@@ -804,6 +831,14 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
                              (int)(c->smem_optin - fd.sharedSizeBytes)) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
     c->near_dyn_max = (int)(c->smem_optin - fnm.sharedSizeBytes);
+    cudaFuncAttributes fhf, fhd;
+    if (cudaFuncGetAttributes(&fhf, k_heur_final<float>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fhd, k_heur_final<double>) != cudaSuccess ||
+        cudaFuncSetAttribute(k_heur_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(c->smem_optin - fhf.sharedSizeBytes)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_heur_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(c->smem_optin - fhd.sharedSizeBytes)) != cudaSuccess)
+      return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
   }
   c->tune.bin_cubes = cfg.bin_cubes;
   c->slots.resize(cfg.max_inflight);

@@ -66,6 +66,8 @@ struct Inst {
   int nbins_cap;
   int* row_cnt;            // surface crossings per hole-map row [rows] (+ROW_UNDECIDED: undecided)
   int* row_x;              // crossings (cube x << 1 | entering) [rows][ROW_XCAP]
+  float* hface;            // truncating variant: face corners, centroid, max |x| [n_faces][16]
+  int hmax_bits;           // truncating variant: largest |face coordinate| (float bits)
   // parameters
   double tol;
   float tol_f;             // tol rounded up to float

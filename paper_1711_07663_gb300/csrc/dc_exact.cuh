@@ -254,6 +254,7 @@ struct WarpState {
   bool near_mode;                    // only decide d(E) <= tol (the side is known)
   bool labeled;                      // the hole map gave the side: ties are not needed
   bool overflow, fringe_done;
+  unsigned fmask;                    // element faces whose triangles take part (bit f; 0x3f: all)
   double d_fringe;
   double dmin64;                     // FP64 minimum over re-solve entries already flushed
 };
@@ -490,13 +491,13 @@ __device__ __noinline__ void process_face(WarpCtx<T>& W, WarpState<T>& S, int f,
   const T Smag = fmax(W.Se, smax);
   const T sigma = (T)C_SIGMA * Eps<T>::u * Smag;
   const T rho = T(2) * Eps<T>::u * Smag;
-  const int nte = W.nte, ntf = W.ntf;
+  const int nte = W.nte, ntf = W.ntf, tpf = nte / 6;
   S.nq = 0;
   for (int t0 = 0; t0 < nte; t0 += 32) {
     // element triangles of this chunk near the face box
     int te = t0 + lane;
     bool near = false;
-    if (te < nte) {
+    if (te < nte && ((S.fmask >> (te / tpf)) & 1u)) {
       T lb = box_dist<T>(W.eb[te], W.eb[nte + te], W.eb[2 * nte + te], W.eb[3 * nte + te], W.eb[4 * nte + te],
                          W.eb[5 * nte + te], flo[0], flo[1], flo[2], fhi[0], fhi[1], fhi[2]);
       near = lb - sigma <= S.Ucert;
@@ -755,6 +756,7 @@ __device__ bool process_element(WarpCtx<T>& W, WarpState<T>& S, ExCounters& cnt)
   S.fringe_done = false;
   S.d_fringe = 0.0;
   S.near_mode = false;
+  S.fmask = 0x3fu;
   S.labeled = any_in != any_out;
   S.dmin64 = INFINITY;
   if (any_in && any_out) {

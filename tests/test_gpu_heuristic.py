@@ -1,0 +1,104 @@
+"""The paper's truncating variant (DC_HEURISTIC) on the GPU through the C ABI,
+against the oracle's version of it (oracle/oracle.c, orc_heuristic): the same
+flags wherever the oracle's decision is unique, the same distances, and the
+same disagreements with the exact cut.
+
+Elements whose box lies within tol of a face box are candidates of every hole
+map, so the variant decides them: their flag must be the oracle variant's
+(or, where an exact tie at a truncation makes several flags possible, one of
+them).  Other elements may be decided by the hole map (exact flag) or by the
+variant, and must carry one of the two."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+dc = None
+HERE = os.path.dirname(os.path.abspath(__file__))
+_spec = importlib.util.spec_from_file_location("necessary_pairs", os.path.join(HERE, "golden", "necessary_pairs.py"))
+NP = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(NP)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global dc
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1711_07663_gb300 as m
+    from paper_1711_07663_gb300 import build as B
+    B.build()
+    m.load()
+    dc = m
+
+
+def check(p, nodes, q, faces, pose=None):
+    n = nodes.shape[0]
+    got = np.empty(n, dtype=np.int8)
+    gd = np.empty(n, dtype=np.float64)
+    with dc.Context([(p, nodes)], precision=dc.DC_HEURISTIC) as ctx:
+        ctx.cut(0, q, faces, got, gd, pose=pose)
+        st = ctx.stats()
+    hf, hs, hd, mg = O.heuristic(p, nodes, q, faces, pose=pose)
+    ef, ed, _, _ = O.cut(p, nodes, q, faces, pose=pose)
+    posed = faces if pose is None else (faces @ np.asarray(pose)[:, :3].T + np.asarray(pose)[:, 3])
+    sure = np.zeros(n, dtype=bool)
+    sure[NP.exact_test_elements(nodes, posed)] = True
+    allowed = ((hs >> (got.astype(np.int16) + 1)) & 1).astype(bool)
+    # FP64-level ties of the first truncation or the corner choice: any flag
+    # the variant or the exact cut gives
+    tie = (mg[:, 0] < 1e-12) | (mg[:, 1] < 1e-12)
+    assert int(tie.sum()) == 0
+    unique = np.array([bin(int(x)).count("1") == 1 for x in hs])
+    assert np.all(allowed[sure]), np.nonzero(sure & ~allowed)[0][:10]
+    assert np.array_equal(got[sure & unique], hf[sure & unique])
+    other = ~sure
+    assert np.all((got[other] == hf[other]) | (got[other] == ef[other]))
+    # distances of the elements the variant decided and did not find fringe
+    same = sure & unique & (hf != O.FRINGE)
+    h = 4.0 / round(n ** (1 / 3))
+    assert np.all(np.abs(gd[same] - hd[same]) <= 1e-12 * np.maximum(np.abs(hd[same]), h))
+    return got, hf, ef, sure, st
+
+
+def test_plain_workload_matches_the_oracle_variant():
+    c = W.sphere_in_box(n=16, p=2, m=8, q=2, seed=1)
+    got, hf, ef, sure, st = check(c.p, c.nodes, c.q, c.faces)
+    assert st["n_candidates"] >= sure.sum()
+    # faces about as large as the elements: the variant loses nothing
+    assert np.array_equal(got, ef)
+
+
+@pytest.mark.parametrize("n,p,m,q,jit", [(6, 1, 32, 1, 0.05), (8, 2, 24, 2, 0.05), (10, 1, 32, 2, 0.2)])
+def test_many_small_faces_reproduce_the_variants_misses(n, p, m, q, jit):
+    nodes = W.background(n, p, jitter=jit, seed=3)
+    faces = W.cubed_sphere(m, q, radius=1.0, centre=(0.03, -0.02, 0.05))
+    got, hf, ef, sure, st = check(p, nodes, q, faces)
+    miss_gpu = (ef == O.FRINGE) & (got != O.FRINGE)
+    miss_orc = (ef == O.FRINGE) & (hf != O.FRINGE)
+    assert miss_orc.sum() > 0
+    assert np.array_equal(miss_gpu[sure], miss_orc[sure])
+    assert not np.any((got == O.FRINGE) & (ef != O.FRINGE))
+
+
+def test_posed_surface_and_batch():
+    cases = W.batch_cases(count=4, seed=8, n_range=(10, 14), m_choices=(16, 24))
+    for cs in cases:
+        check(cs.p, cs.nodes, cs.q, cs.faces, pose=cs.pose)
+    # the same instances in one batched cut give the same flags
+    outs = [np.empty(cs.n_elem, dtype=np.int8) for cs in cases]
+    single = []
+    with dc.Context([(cs.p, cs.nodes) for cs in cases], precision=dc.DC_HEURISTIC) as ctx:
+        ctx.cut_batch(list(range(len(cases))),
+                      [dict(q=cs.q, faces=cs.faces, flags_out=o, pose=cs.pose) for cs, o in zip(cases, outs)])
+        for i, cs in enumerate(cases):
+            single.append(ctx.cut(i, cs.q, cs.faces, pose=cs.pose))
+    for a, b in zip(outs, single):
+        assert np.array_equal(a, b)

@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--heuristic-steps", type=int, default=10,
+                    help="timed cuts of the paper's truncating variant (0: skip it)")
     ap.add_argument("--workload", default="scale64", choices=sorted(WORKLOADS),
                     help="scale64 is the benchmark; the others are small cases for profiling")
     return ap.parse_args()
@@ -357,6 +359,32 @@ def run_ours(args, world, rank, local):
         if k >= args.warmup:
             ub_ms.append(a.elapsed_time(b))
 
+    # the paper's truncating variant on the same workload: its time and how
+    # many flags differ from the exact cut (flags of the timed loop above)
+    heur = None
+    if args.heuristic_steps > 0:
+        hflags = torch.empty_like(flags)
+        with dc.Context([(case.p, nodes)], precision=dc.DC_HEURISTIC, device=local) as hctx:
+            for _ in range(2):
+                hctx.cut(0, case.q, faces, hflags, stream=stream.cuda_stream)
+            hms = []
+            for k in range(args.heuristic_steps):
+                flush.fill_(k & 0xff)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                hctx.cut(0, case.q, faces, hflags, stream=stream.cuda_stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                hms.append(a.elapsed_time(b))
+            hst = hctx.stats()
+        ex, hv = flags.cpu().numpy(), hflags.cpu().numpy()
+        heur = {"ms": float(np.median(hms)), "disagree": int((ex != hv).sum()),
+                "missed_fringe": int(((ex == dc.DC_FRINGE) & (hv != dc.DC_FRINGE)).sum()),
+                "false_fringe": int(((ex != dc.DC_FRINGE) & (hv == dc.DC_FRINGE)).sum()),
+                "side_differs": int(((ex != dc.DC_FRINGE) & (hv != dc.DC_FRINGE) & (ex != hv)).sum()),
+                "fp64_key_rescans": hst["heur_rescans"], "fp64_pass1_resolves": hst["heur_resolves"]}
+
     # roofline of the dominant kernel (the flags-only exact stage): ALU bound.
     # Algorithmic arithmetic = the exact test on the necessary pair set S*:
     # |S*| x n_Tc x n_T(F) triangle pairs x the flops of one triangle pair, with
@@ -401,6 +429,7 @@ def run_ours(args, world, rank, local):
             "plain_same_flags": same_flags,
             "unblank_step_ms": float(np.median(ub_ms)),
             "tuning": None if tuning is None else dict(tuning, trials=tune_trials),
+            "paper_truncating_variant": heur,
             "phases_ms": {"surface_bins": float(np.mean(surf_ms)), "holemap": float(np.mean(hm_ms)),
                           "classify": float(np.mean(cls_ms)), "exact_fp32": ex_ms, "redo_fp64": float(np.mean(redo_ms)),
                           "library_total": float(np.mean(total_ms)),

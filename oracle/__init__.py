@@ -72,6 +72,14 @@ def lib():
             L.orc_approx_dist.argtypes = [P, P, P, P]
             L.orc_pass1.restype = d
             L.orc_pass1.argtypes = [i32, P, i32, P, d, ctypes.POINTER(i32), ctypes.POINTER(d)]
+            L.orc_lagrange.restype = None
+            L.orc_lagrange.argtypes = [i32, d, P, P]
+            L.orc_map.restype = None
+            L.orc_map.argtypes = [i32, P, P, P, P]
+            L.orc_newton.restype = i32
+            L.orc_newton.argtypes = [i32, P, P, d, P, ctypes.POINTER(d), ctypes.POINTER(i32)]
+            L.orc_locate.restype = i32
+            L.orc_locate.argtypes = [i32, i64, P, i64, P, P, P, P, P, i32]
             L.orc_heuristic.restype = i32
             L.orc_heuristic.argtypes = [i32, i64, P, i32, i64, P, P, d, i32, i32, P, i64, P, P, P, P, i32]
             _lib = L
@@ -229,3 +237,45 @@ def heuristic(p, nodes, q, faces, pose=None, tol=1e-7, nf1=16, nf2=4, ids=None, 
     if rc != 0:
         raise ValueError("orc_heuristic rejected its arguments")
     return flags, fset, dist, margins
+
+
+# ----------------------------------------------------------------- donor search (point connectivity)
+def lagrange(p, x):
+    """Lagrange basis on the p+1 equispaced nodes of [-1,1] at x: (l, dl/dx)."""
+    l, dl = np.zeros(p + 1), np.zeros(p + 1)
+    lib().orc_lagrange(p, float(x), _ptr(l), _ptr(dl))
+    return l, dl
+
+
+def iso_map(p, enodes, xi):
+    """x(xi) and the Jacobian dx/dxi (3x3, row = component) of one element."""
+    enodes, xi = _f64(enodes), _f64(xi)
+    x, J = np.zeros(3), np.zeros(9)
+    lib().orc_map(p, _ptr(enodes), _ptr(xi), _ptr(x), _ptr(J))
+    return x, J.reshape(3, 3)
+
+
+def newton(p, enodes, x, h):
+    """The clamped Newton inversion from xi = 0: (converged, xi, residual, iterations)."""
+    enodes, x = _f64(enodes), _f64(x)
+    xi = np.zeros(3)
+    r = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    ok = lib().orc_newton(p, _ptr(enodes), _ptr(x), float(h), _ptr(xi), ctypes.byref(r), ctypes.byref(it))
+    return bool(ok), xi, r.value, it.value
+
+
+def locate(p, nodes, pts, pose=None, nthreads=0):
+    """Donor element (-1: none) and reference coordinates of each point, and
+    the acceptance margins [n][2] (residual gap, reference gap)."""
+    nodes, pts = _f64(nodes), _f64(pts).reshape(-1, 3)
+    n = pts.shape[0]
+    donor = np.zeros(n, dtype=np.int64)
+    ref = np.zeros((n, 3))
+    margins = np.zeros((n, 2))
+    pose_arr = None if pose is None else _f64(np.asarray(pose).reshape(3, 4))
+    rc = lib().orc_locate(p, nodes.shape[0], _ptr(nodes), n, _ptr(pts), _ptr(pose_arr), _ptr(donor), _ptr(ref),
+                          _ptr(margins), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_locate rejected its arguments")
+    return donor, ref, margins

@@ -41,6 +41,10 @@
  * unpinned (the paper gives no reference output for it), and is what the tests
  * measure against the exact result above.
  *
+ * The donor search of the point-connectivity step (orc_locate, end of file)
+ * is the plain definition: every element whose box holds the point, in index
+ * order, then the paper's clamped Newton inversion of the isoparametric map.
+ *
  * Compile with -ffp-contract=off so a*b+c is never fused: the pose transform
  * below must round exactly like the element-wise form it is written in.
  */
@@ -805,7 +809,7 @@ int orc_heuristic(int p, int64_t n_elem, const double *nodes, int q, int64_t n_f
     if (p < 1 || q < 1 || n_elem < 0 || n_faces < 1 || !nodes || !faces || nf1 < 1 || nf2 < 1 || nf2 > nf1 || nf1 > 64)
         return -1;
     const int npe = (p + 1) * (p + 1) * (p + 1), npf = (q + 1) * (q + 1);
-    const int nte = 12 * p * p, ntf = 2 * q * q, tpf = 2 * p * p;
+    const int nte = 12 * p * p, ntf = 2 * q * q;
     const int64_t nts = n_faces * ntf;
     const int64_t nev = ids ? n_ids : n_elem;
     double *fx = (double *)malloc(sizeof(double) * 3 * npf * n_faces);
@@ -916,5 +920,149 @@ int orc_heuristic(int p, int64_t n_elem, const double *nodes, int q, int64_t n_f
     free(fx);
     free(stris);
     free(fcorn);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* donor search for receptor points (Sec. "Donor/Receptor Point             */
+/* Connectivity on GPUs", Eqs. reftophys, ref-update, Jac)                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * For each point x_p (world frame) and a donor grid of order-p hexes moved
+ * rigidly by pose [R|t] (initial frame -> world; NULL: identity):
+ *   1. the point in the grid's initial frame: x = R^T (x_p - t);
+ *   2. every element whose node box contains x (brute force over all
+ *      elements, in index order; the ADT of the paper only finds these
+ *      faster);
+ *   3. Newton on the isoparametric map x(xi) = sum_ijk x_ijk l_i(xi) l_j(eta)
+ *      l_k(zeta) (Lagrange basis on the p+1 equispaced nodes of [-1,1]):
+ *      xi^0 = 0, xi^{n+1} = xi^n + J^{-1}(xi^n) (x - x(xi^n)), each component
+ *      clamped to [-1 - 1e-4, 1 + 1e-4], at most 10 iterations, stopping when
+ *      |x - x(xi)| <= 1e-10 h (h: the element box's largest side);
+ *   4. the donor is the first element (lowest index) where the iteration
+ *      stopped that way with max |xi_a| <= 1 + 1e-8; its xi is returned.
+ *      No such element: donor -1.
+ * margins[2] per point: residual gap (1e-10 h - |x - x(xi)|) and reference
+ * gap (1 + 1e-8 - max |xi_a|) of the returned donor (of the last element
+ * tried when none is found), how close its acceptance was to flipping.
+ */
+#define ORC_NEWTON_ITERS 10
+#define ORC_NEWTON_CLAMP 1e-4
+#define ORC_INSIDE_TOL 1e-8
+#define ORC_RESID_REL 1e-10
+
+/* Lagrange basis on equispaced nodes of [-1,1] and its derivative */
+void orc_lagrange(int p, double x, double *l, double *dl) {
+    double nd[8];
+    for (int i = 0; i <= p; ++i) nd[i] = -1.0 + 2.0 * i / p;
+    for (int i = 0; i <= p; ++i) {
+        double v = 1.0, dv = 0.0;
+        for (int j = 0; j <= p; ++j) {
+            if (j == i) continue;
+            const double inv = 1.0 / (nd[i] - nd[j]);
+            dv = dv * (x - nd[j]) * inv + v * inv;   /* product rule, left to right */
+            v *= (x - nd[j]) * inv;
+        }
+        l[i] = v;
+        if (dl) dl[i] = dv;
+    }
+}
+
+/* x(xi) and the Jacobian d x / d xi (row a: component a) of one element */
+void orc_map(int p, const double *en, const double *xi, double *x, double *J) {
+    double lx[8], ly[8], lz[8], dx[8], dy[8], dz[8];
+    orc_lagrange(p, xi[0], lx, dx);
+    orc_lagrange(p, xi[1], ly, dy);
+    orc_lagrange(p, xi[2], lz, dz);
+    for (int a = 0; a < 3; ++a) { x[a] = 0.0; if (J) J[3 * a] = J[3 * a + 1] = J[3 * a + 2] = 0.0; }
+    for (int k = 0; k <= p; ++k)
+        for (int j = 0; j <= p; ++j)
+            for (int i = 0; i <= p; ++i) {
+                const double *X = en + 3 * node_index(p, i, j, k);
+                const double N = lx[i] * ly[j] * lz[k];
+                const double Nx = dx[i] * ly[j] * lz[k], Ny = lx[i] * dy[j] * lz[k], Nz = lx[i] * ly[j] * dz[k];
+                for (int a = 0; a < 3; ++a) {
+                    x[a] += X[a] * N;
+                    if (J) { J[3 * a] += X[a] * Nx; J[3 * a + 1] += X[a] * Ny; J[3 * a + 2] += X[a] * Nz; }
+                }
+            }
+}
+
+/* solve J d = r (3x3, Cramer's rule); 0 when J is singular */
+static int solve3(const double *J, const double *r, double *d) {
+    const double c00 = J[4] * J[8] - J[5] * J[7], c01 = J[5] * J[6] - J[3] * J[8], c02 = J[3] * J[7] - J[4] * J[6];
+    const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+    if (!(fabs(det) > 0.0)) return 0;
+    const double inv = 1.0 / det;
+    d[0] = (r[0] * c00 + r[1] * (J[2] * J[7] - J[1] * J[8]) + r[2] * (J[1] * J[5] - J[2] * J[4])) * inv;
+    d[1] = (r[0] * c01 + r[1] * (J[0] * J[8] - J[2] * J[6]) + r[2] * (J[2] * J[3] - J[0] * J[5])) * inv;
+    d[2] = (r[0] * c02 + r[1] * (J[1] * J[6] - J[0] * J[7]) + r[2] * (J[0] * J[4] - J[1] * J[3])) * inv;
+    return 1;
+}
+
+/* Eq. ref-update from xi = 0: returns 1 when the residual fell within
+ * 1e-10 h; xi, the last residual norm and the iteration count out */
+int orc_newton(int p, const double *en, const double *x, double h, double *xi, double *resid, int *iters) {
+    xi[0] = xi[1] = xi[2] = 0.0;
+    const double lim = 1.0 + ORC_NEWTON_CLAMP, tolx = ORC_RESID_REL * h;
+    double X[3], J[9], r[3], d[3];
+    int n = 0;
+    for (;;) {
+        orc_map(p, en, xi, X, J);
+        for (int a = 0; a < 3; ++a) r[a] = x[a] - X[a];
+        const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        *resid = rn;
+        *iters = n;
+        if (rn <= tolx) return 1;
+        if (n == ORC_NEWTON_ITERS || !solve3(J, r, d)) return 0;
+        for (int a = 0; a < 3; ++a) {
+            double v = xi[a] + d[a];
+            xi[a] = v < -lim ? -lim : (v > lim ? lim : v);
+        }
+        ++n;
+    }
+}
+
+int orc_locate(int p, int64_t n_elem, const double *nodes, int64_t n_pts, const double *pts, const double *pose,
+               int64_t *donor, double *ref, double *margins, int nthreads) {
+    if (p < 1 || p > 7 || n_elem < 1 || n_pts < 0 || !nodes || !pts) return -1;
+    const int npe = (p + 1) * (p + 1) * (p + 1);
+    double *box = (double *)malloc(sizeof(double) * 6 * n_elem);
+    for (int64_t e = 0; e < n_elem; ++e) aabb_of(nodes + 3 * npe * e, npe, box + 6 * e);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_pts; ++k) {
+        const double *P = pts + 3 * k;
+        double x[3];
+        if (pose) {
+            const double q[3] = {P[0] - pose[3], P[1] - pose[7], P[2] - pose[11]};
+            for (int a = 0; a < 3; ++a) x[a] = (pose[a] * q[0] + pose[4 + a] * q[1]) + pose[8 + a] * q[2];
+        } else {
+            x[0] = P[0]; x[1] = P[1]; x[2] = P[2];
+        }
+        int64_t found = -1;
+        double xi[3] = {0, 0, 0}, m[2] = {-INFINITY, -INFINITY};
+        for (int64_t e = 0; e < n_elem && found < 0; ++e) {
+            const double *b = box + 6 * e;
+            if (x[0] < b[0] || x[0] > b[3] || x[1] < b[1] || x[1] > b[4] || x[2] < b[2] || x[2] > b[5]) continue;
+            const double h = fmax(b[3] - b[0], fmax(b[4] - b[1], b[5] - b[2]));
+            double t[3], rn;
+            int it;
+            const int conv = orc_newton(p, nodes + 3 * npe * e, x, h, t, &rn, &it);
+            const double mx = fmax(fabs(t[0]), fmax(fabs(t[1]), fabs(t[2])));
+            m[0] = ORC_RESID_REL * h - rn;
+            m[1] = 1.0 + ORC_INSIDE_TOL - mx;
+            if (conv && mx <= 1.0 + ORC_INSIDE_TOL) {
+                found = e;
+                xi[0] = t[0]; xi[1] = t[1]; xi[2] = t[2];
+            }
+        }
+        donor[k] = found;
+        if (ref) { ref[3 * k] = xi[0]; ref[3 * k + 1] = xi[1]; ref[3 * k + 2] = xi[2]; }
+        if (margins) { margins[2 * k] = m[0]; margins[2 * k + 1] = m[1]; }
+    }
+    free(box);
     return 0;
 }

@@ -277,6 +277,35 @@ def cubed_sphere(n: int, q: int, *, radius: float = 1.0, centre=(0.0, 0.0, 0.0),
     return np.ascontiguousarray(X)
 
 
+def sphere_shell(n: int, layers: int, p: int, r0: float = 1.0, r1: float = 1.6, centre=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """A body-fitted near-body grid around a sphere: 6*n*n*layers order-p hexes
+    filling r0 <= r <= r1 (cubed-sphere cells x radial layers), float64
+    [E][(p+1)^3][3] in tensor order (i, j along the cube-face cell, k radial).
+    Node radii are equispaced; directions are the cubed-sphere lattice points,
+    so neighbouring elements share identical nodes."""
+    P = cube_face_points(n, p).astype(np.float64)
+    nrm = np.sqrt(P[..., 0] * P[..., 0] + P[..., 1] * P[..., 1] + P[..., 2] * P[..., 2])
+    xhat = P / nrm[..., None]                                  # [6n^2][(p+1)^2][3]
+    kk = np.arange(layers * p + 1, dtype=np.float64)
+    radii = r0 + (r1 - r0) * kk / (layers * p)
+    out = np.empty((xhat.shape[0], layers, p + 1, (p + 1) ** 2, 3), dtype=np.float64)
+    for L in range(layers):
+        for k in range(p + 1):
+            out[:, L, k] = xhat * radii[L * p + k]
+    out = out.reshape(xhat.shape[0] * layers, (p + 1) ** 3, 3)
+    return np.ascontiguousarray(out + np.asarray(centre, dtype=np.float64))
+
+
+def shell_points(count: int, r0: float, r1: float, seed: int, centre=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Seeded points spread over the shell r0 <= r <= r1 (uniform direction,
+    uniform radius): float64 [count][3]."""
+    g = rng(seed)
+    d = g.normal(size=(count, 3))
+    d /= np.sqrt((d * d).sum(axis=1))[:, None]
+    r = g.uniform(r0, r1, size=count)
+    return np.ascontiguousarray(d * r[:, None] + np.asarray(centre, dtype=np.float64))
+
+
 def box_surface(lo, hi, n: int = 1, q: int = 1) -> np.ndarray:
     """Outward-oriented axis-aligned box [lo,hi] as 6*n*n order-q faces (used by
     tests for flat and concave geometry)."""

@@ -299,6 +299,56 @@ dc_status dc_unblank(int32_t kind, int64_t n_elem, const int8_t *iblank_prev, co
 /* Library version string. */
 const char *dc_version(void);
 
+/* ------------------------------------------------------------------------
+ * Point connectivity: donors for receptor points (after the cut)
+ * ------------------------------------------------------------------------
+ * Sec. "Donor/Receptor Point Connectivity on GPUs": the flux points of the
+ * artificial-boundary faces of one grid need a donor element of another grid
+ * and their reference coordinates in it.  dc_pc_create builds, once, a
+ * balanced search tree over the donor grid's element boxes on the host (one
+ * element per node, median splits over the six box coordinates in turn, as
+ * an alternating digital tree) and copies it with the grid to the device.
+ * The grid may then move rigidly: dc_pc_locate takes each point into the
+ * grid's initial frame with the inverse of `pose` instead of rebuilding the
+ * tree, finds the elements whose node box holds it by a depth-first traversal
+ * with a fixed stack (32 entries), and checks them in index order with the
+ * clamped Newton inversion of the isoparametric map (Eq. ref-update: from
+ * xi = 0, xi clamped to [-1 - 1e-4, 1 + 1e-4], at most 10 FP32 steps in the
+ * element frame, then FP64 steps on the original nodes).  A point's donor is
+ * the first (lowest-index) element where the residual falls to 1e-10 h (h:
+ * the element box's largest side) with max |xi_a| <= 1 + 1e-8; otherwise -1.
+ * Lagrange nodes are equispaced on [-1, 1] (tensor order, xi fastest). */
+typedef struct dc_pc dc_pc;
+
+typedef struct {
+    int64_t n_points;         /* points of the last dc_pc_locate */
+    int64_t n_found;          /* ... with a donor */
+    int64_t candidates;       /* element boxes that held a point (Newton solves tried) */
+    int64_t fp64_steps;       /* FP64 Newton steps after the FP32 stage */
+    int64_t tree_depth;       /* levels of the search tree */
+} dc_pc_stats;
+
+/* Copy a donor grid of n_elem order-p hexes (p 1..4; nodes [n_elem][(p+1)^3][3],
+ * host or device pointer) to `device` and build its search tree.  DC_EINVAL
+ * for bad sizes or a non-finite node. */
+dc_status dc_pc_create(int32_t device, int32_t p, int64_t n_elem, const double *nodes, int32_t nodes_on_device,
+                       dc_pc **out);
+
+/* Donors of n_pts points pts [n_pts][3] (world frame).  pose: 12 doubles
+ * [R|t], the grid's rigid motion from its initial frame (NULL: none).
+ * donor_out [n_pts] (-1: no donor), ref_out [n_pts][3] reference coordinates
+ * (0 when none).  on_device: all three arrays are device pointers (else host).
+ * Synchronous on `stream` (NULL: the context's own).  DC_EINTERNAL when a
+ * point lies in more than 16 element boxes (its answer is then incomplete). */
+dc_status dc_pc_locate(dc_pc *pc, int64_t n_pts, const double *pts, const double *pose, int64_t *donor_out,
+                       double *ref_out, int32_t on_device, void *stream);
+
+/* Counters of the last dc_pc_locate. */
+dc_status dc_pc_get_stats(dc_pc *pc, dc_pc_stats *out);
+
+/* Free the donor grid and its tree. */
+void dc_pc_destroy(dc_pc *pc);
+
 #ifdef __cplusplus
 }
 #endif

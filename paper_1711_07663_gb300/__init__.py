@@ -24,7 +24,7 @@ __all__ = [
     "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
     "dc_last_error", "dc_version", "dc_cut_noalloc", "Context", "EXPORTED",
     "DC_WALL", "DC_OVERSET", "dc_blank_union", "dc_ab_faces", "dc_unblank", "structured_neighbours",
-    "dc_get_tuning", "dc_set_tuning", "dc_autotune",
+    "dc_get_tuning", "dc_set_tuning", "dc_autotune", "PointLocator",
 ]
 
 DC_OK, DC_PENDING = 0, 1
@@ -34,7 +34,8 @@ DC_FP64, DC_FP32_RECHECK, DC_HEURISTIC = 0, 1, 2
 
 EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
             "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc", "dc_blank_union", "dc_ab_faces",
-            "dc_unblank", "dc_get_tuning", "dc_set_tuning", "dc_autotune")
+            "dc_unblank", "dc_get_tuning", "dc_set_tuning", "dc_autotune", "dc_pc_create", "dc_pc_locate",
+            "dc_pc_get_stats", "dc_pc_destroy")
 DC_WALL, DC_OVERSET = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -80,6 +81,10 @@ class dc_stats(ctypes.Structure):
 class dc_tuning(ctypes.Structure):
     _fields_ = [("cubes_per_edge", ctypes.c_float), ("bin_cubes", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("cands_per_warp", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class dc_pc_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_points", "n_found", "candidates", "fp64_steps", "tree_depth")]
 
 
 _lib = None
@@ -136,6 +141,14 @@ def load(build_if_missing: bool = False):
         L.dc_autotune.argtypes = [P, i32, ctypes.POINTER(i32), ctypes.POINTER(dc_request), i32,
                                   ctypes.POINTER(dc_tuning), ctypes.POINTER(i32)]
         L.dc_autotune.restype = i32
+        L.dc_pc_create.argtypes = [i32, i32, i64, P, i32, ctypes.POINTER(P)]
+        L.dc_pc_create.restype = i32
+        L.dc_pc_locate.argtypes = [P, i64, P, P, P, P, i32, P]
+        L.dc_pc_locate.restype = i32
+        L.dc_pc_get_stats.argtypes = [P, ctypes.POINTER(dc_pc_stats)]
+        L.dc_pc_get_stats.restype = i32
+        L.dc_pc_destroy.argtypes = [P]
+        L.dc_pc_destroy.restype = None
         _lib = L
         return L
 
@@ -367,6 +380,61 @@ def dc_autotune(ctx, meshes, requests, repeats=3):
     trials = ctypes.c_int32(0)
     _check(load().dc_autotune(ctx, n, ms, arr, int(repeats), ctypes.byref(best), ctypes.byref(trials)))
     return _tuning_dict(best), trials.value
+
+
+class PointLocator:
+    """Donor search on one grid: PointLocator(p, nodes[, device]); locate(pts,
+    pose=None) -> (donor int64 [n], ref float64 [n][3]) for host arrays, or
+    writes into given device tensors."""
+
+    def __init__(self, p, nodes, device=0):
+        np_, ndev, keep = _addr(nodes, np.float64)
+        h = ctypes.c_void_p()
+        _check(load().dc_pc_create(int(device), int(p), int(keep.shape[0]), np_, int(ndev), ctypes.byref(h)))
+        self.handle = h
+        self.n_elem = int(keep.shape[0])
+
+    def locate(self, pts, pose=None, donor_out=None, ref_out=None, stream=None):
+        pp, pdev, pk = _addr(pts, np.float64)
+        n = int(pk.shape[0]) if pk.ndim > 1 else int(pk.shape[0]) // 3
+        if donor_out is None:
+            if pdev:
+                import torch
+                donor_out = torch.empty(n, dtype=torch.int64, device=pts.device)
+                ref_out = torch.empty((n, 3), dtype=torch.float64, device=pts.device)
+            else:
+                donor_out = np.empty(n, dtype=np.int64)
+                ref_out = np.empty((n, 3), dtype=np.float64)
+        dp, ddev, dk = _addr(donor_out, np.int64)
+        rp, rdev, rk = _addr(ref_out, np.float64)
+        if not (pdev == ddev == rdev):
+            raise ValueError("points, donor_out and ref_out must all be host arrays or all device tensors")
+        pk_ = None if pose is None else np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
+        _check(load().dc_pc_locate(self.handle, n, pp, None if pk_ is None else pk_.ctypes.data, dp, rp, int(pdev),
+                                   None if stream is None else int(stream)))
+        return donor_out, ref_out
+
+    def stats(self):
+        s = dc_pc_stats()
+        _check(load().dc_pc_get_stats(self.handle, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in dc_pc_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().dc_pc_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

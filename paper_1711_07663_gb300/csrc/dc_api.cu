@@ -23,6 +23,7 @@
 #include "dc_near.cuh"
 #include "dc_overset.cuh"
 #include "dc_heur.cuh"
+#include "dc_pc.cuh"
 
 using namespace dc;
 
@@ -1393,6 +1394,263 @@ dc_status dc_unblank(int32_t kind, int64_t n_elem, const int8_t* iblank_prev, co
   CK(cudaStreamSynchronize(st));
   if (n_unblank) *n_unblank = (int64_t)h;
   return DC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- point connectivity
+struct dc_pc {
+  int device = 0, p = 0, n_sm = 0, root = -1, depth = 0;
+  long long n_elem = 0;
+  double* nodes = nullptr;
+  float* loc = nullptr;
+  double* org = nullptr;
+  float* fbox = nullptr;
+  double* ebox = nullptr;
+  float* h = nullptr;
+  PcNode* tree = nullptr;
+  cudaStream_t stream = nullptr;
+  size_t cap = 0;  // points the scratch below holds
+  double *pts = nullptr, *xloc = nullptr, *ref = nullptr;
+  int *ncand = nullptr, *cand = nullptr;
+  long long* donor = nullptr;
+  unsigned long long* cnt = nullptr;
+  dc_pc_stats last{};
+  std::mutex mu;
+};
+
+namespace {
+
+float round_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float round_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// balanced tree over the element boxes: the median of box coordinate
+// (depth mod 6) of (min x, min y, min z, max x, max y, max z) splits each
+// range; returns the node index (-1: empty range)
+int pc_build(std::vector<PcNode>& T, std::vector<int>& idx, int lo, int hi, int depth, const std::vector<double>& box,
+             int& maxdepth) {
+  if (lo >= hi) return -1;
+  maxdepth = std::max(maxdepth, depth + 1);
+  const int axis = depth % 6, mid = lo + (hi - lo) / 2;
+  std::nth_element(idx.begin() + lo, idx.begin() + mid, idx.begin() + hi, [&](int a, int b) {
+    const double ka = box[6 * (size_t)a + axis], kb = box[6 * (size_t)b + axis];
+    return ka < kb || (ka == kb && a < b);
+  });
+  const int node = (int)T.size();
+  T.emplace_back();
+  const int e = idx[mid];
+  const int l = pc_build(T, idx, lo, mid, depth + 1, box, maxdepth);
+  const int r = pc_build(T, idx, mid + 1, hi, depth + 1, box, maxdepth);
+  PcNode& N = T[node];
+  N.elem = e;
+  N.left = l;
+  N.right = r;
+  N.pad = 0;
+  for (int a = 0; a < 3; ++a) {
+    N.elo[a] = round_down(box[6 * (size_t)e + a]);
+    N.ehi[a] = round_up(box[6 * (size_t)e + 3 + a]);
+    N.slo[a] = N.elo[a];
+    N.shi[a] = N.ehi[a];
+    for (int c : {l, r})
+      if (c >= 0) {
+        N.slo[a] = std::min(N.slo[a], T[c].slo[a]);
+        N.shi[a] = std::max(N.shi[a], T[c].shi[a]);
+      }
+  }
+  return node;
+}
+
+void pc_free(dc_pc* pc) {
+  for (void* q : std::initializer_list<void*>{pc->nodes, pc->loc, pc->org, pc->fbox, pc->ebox, pc->h, pc->tree, pc->pts,
+                                              pc->xloc, pc->ref, pc->ncand, pc->cand, pc->donor, pc->cnt})
+    if (q) cudaFree(q);
+  if (pc->stream) cudaStreamDestroy(pc->stream);
+  delete pc;
+}
+
+dc_status pc_reserve(dc_pc* pc, size_t n) {
+  if (pc->cap >= n) return DC_OK;
+  const size_t m = std::max(n, pc->cap + pc->cap / 2);
+  for (void* q : std::initializer_list<void*>{pc->pts, pc->xloc, pc->ref, pc->ncand, pc->cand, pc->donor})
+    if (q) cudaFree(q);
+  pc->pts = pc->xloc = pc->ref = nullptr;
+  pc->ncand = pc->cand = nullptr;
+  pc->donor = nullptr;
+  pc->cap = 0;
+  if (cudaMalloc(&pc->pts, sizeof(double) * 3 * m) != cudaSuccess ||
+      cudaMalloc(&pc->xloc, sizeof(double) * 3 * m) != cudaSuccess ||
+      cudaMalloc(&pc->ref, sizeof(double) * 3 * m) != cudaSuccess || cudaMalloc(&pc->ncand, sizeof(int) * m) != cudaSuccess ||
+      cudaMalloc(&pc->cand, sizeof(int) * PC_CAND * m) != cudaSuccess ||
+      cudaMalloc(&pc->donor, sizeof(long long) * m) != cudaSuccess)
+    return fail(DC_ENOMEM, "point scratch for %zu points: cudaMalloc failed", m);
+  pc->cap = m;
+  return DC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dc_status dc_pc_create(int32_t device, int32_t p, int64_t n_elem, const double* nodes, int32_t nodes_on_device,
+                       dc_pc** out) {
+  g_err.clear();
+  if (!out) return fail(DC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (p < 1 || p > PC_MAXP) return fail(DC_EINVAL, "order p=%d outside 1..%d", p, PC_MAXP);
+  if (n_elem < 1 || n_elem >= (1LL << 31) - 1) return fail(DC_EINVAL, "n_elem=%lld out of range", (long long)n_elem);
+  if (!nodes) return fail(DC_EINVAL, "nodes is NULL");
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(DC_EINVAL, "device %d does not exist", device);
+  CK(cudaSetDevice(device));
+  const int npe = (p + 1) * (p + 1) * (p + 1);
+  const size_t nn = (size_t)n_elem * npe * 3;
+  std::vector<double> hn;
+  const double* hp = nodes;
+  if (nodes_on_device) {
+    hn.resize(nn);
+    CK(cudaMemcpy(hn.data(), nodes, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+    hp = hn.data();
+  }
+  // FP64 boxes, sizes, the tree (host)
+  std::vector<double> box(6 * (size_t)n_elem);
+  std::vector<float> hs((size_t)n_elem);
+  for (long long e = 0; e < n_elem; ++e) {
+    const double* x = hp + (size_t)e * npe * 3;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = 0; k < npe; ++k)
+      for (int a = 0; a < 3; ++a) {
+        const double v = x[3 * k + a];
+        if (!std::isfinite(v)) return fail(DC_EINVAL, "element %lld has a NaN or infinite node", e);
+        lo[a] = std::min(lo[a], v);
+        hi[a] = std::max(hi[a], v);
+      }
+    for (int a = 0; a < 3; ++a) { box[6 * e + a] = lo[a]; box[6 * e + 3 + a] = hi[a]; }
+    hs[e] = (float)std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  }
+  std::vector<PcNode> T;
+  T.reserve((size_t)n_elem);
+  std::vector<int> idx((size_t)n_elem);
+  for (long long e = 0; e < n_elem; ++e) idx[e] = (int)e;
+  int depth = 0;
+  const int root = pc_build(T, idx, 0, (int)n_elem, 0, box, depth);
+  if (depth > PC_STACK) return fail(DC_EINVAL, "search tree depth %d exceeds the traversal stack", depth);
+  dc_pc* pc = new dc_pc();
+  pc->device = device;
+  pc->p = p;
+  pc->n_elem = n_elem;
+  pc->root = root;
+  pc->depth = depth;
+  auto bail = [&](dc_status st) { pc_free(pc); return st; };
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaGetDeviceProperties failed"));
+  pc->n_sm = prop.multiProcessorCount;
+  if (cudaStreamCreateWithFlags(&pc->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&pc->nodes, sizeof(double) * nn) != cudaSuccess ||
+      cudaMalloc(&pc->loc, sizeof(float) * nn) != cudaSuccess ||
+      cudaMalloc(&pc->org, sizeof(double) * 3 * n_elem) != cudaSuccess ||
+      cudaMalloc(&pc->fbox, sizeof(float) * 6 * n_elem) != cudaSuccess ||
+      cudaMalloc(&pc->ebox, sizeof(double) * 6 * n_elem) != cudaSuccess ||
+      cudaMalloc(&pc->h, sizeof(float) * n_elem) != cudaSuccess ||
+      cudaMalloc(&pc->tree, sizeof(PcNode) * T.size()) != cudaSuccess ||
+      cudaMalloc(&pc->cnt, sizeof(unsigned long long) * 4) != cudaSuccess)
+    return bail(fail(DC_ENOMEM, "donor grid of %lld elements: cudaMalloc failed", (long long)n_elem));
+  cudaStream_t st = pc->stream;
+  if (cudaMemcpyAsync(pc->nodes, nodes, sizeof(double) * nn,
+                      nodes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(pc->ebox, box.data(), sizeof(double) * box.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(pc->h, hs.data(), sizeof(float) * hs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(pc->tree, T.data(), sizeof(PcNode) * T.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return bail(fail(DC_ECUDA, "uploading the donor grid failed"));
+  int* d_bad = nullptr;
+  if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  k_elem_box<<<(unsigned)((n_elem + 255) / 256), 256, 0, st>>>(pc->nodes, (long long)n_elem, npe, pc->fbox, pc->loc,
+                                                                  pc->org, d_bad, nullptr);
+  const cudaError_t ke = cudaStreamSynchronize(st);
+  cudaFree(d_bad);
+  if (ke != cudaSuccess) return bail(fail(DC_ECUDA, "element frames failed: %s", cudaGetErrorString(ke)));
+  *out = pc;
+  return DC_OK;
+}
+
+dc_status dc_pc_locate(dc_pc* pc, int64_t n_pts, const double* pts, const double* pose, int64_t* donor_out,
+                       double* ref_out, int32_t on_device, void* stream) {
+  g_err.clear();
+  if (!pc) return fail(DC_EINVAL, "pc is NULL");
+  if (n_pts < 0) return fail(DC_EINVAL, "n_pts < 0");
+  if (n_pts > 0 && (!pts || !donor_out || !ref_out)) return fail(DC_EINVAL, "NULL argument");
+  if (pose)
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(pose[i])) return fail(DC_EINVAL, "pose has a non-finite entry");
+  std::lock_guard<std::mutex> lk(pc->mu);
+  CK(cudaSetDevice(pc->device));
+  pc->last = dc_pc_stats{};
+  pc->last.n_points = n_pts;
+  if (n_pts == 0) return DC_OK;
+  dc_status rc = pc_reserve(pc, (size_t)n_pts);
+  if (rc) return rc;
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : pc->stream;
+  PcGrid G{pc->p, pc->n_elem, pc->nodes, pc->loc, pc->org, pc->ebox, pc->h, pc->tree, pc->root};
+  PcQuery Q{};
+  Q.n = n_pts;
+  if (on_device) {
+    Q.pts = pts;
+  } else {
+    CK(cudaMemcpyAsync(pc->pts, pts, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, st));
+    Q.pts = pc->pts;
+  }
+  Q.has_pose = pose ? 1 : 0;
+  if (pose) memcpy(Q.pose, pose, sizeof(Q.pose));
+  Q.xloc = pc->xloc;
+  Q.ncand = pc->ncand;
+  Q.cand = pc->cand;
+  Q.donor = on_device ? reinterpret_cast<long long*>(donor_out) : pc->donor;
+  Q.ref = on_device ? ref_out : pc->ref;
+  Q.cnt = pc->cnt;
+  CK(cudaMemsetAsync(pc->cnt, 0, sizeof(unsigned long long) * 4, st));
+  const unsigned gs = (unsigned)std::min<long long>((n_pts + 255) / 256, (long long)pc->n_sm * 16);
+  k_pc_search<<<gs, 256, 0, st>>>(G, Q);
+  CK(cudaGetLastError());
+  const unsigned gn = (unsigned)std::min<long long>((n_pts + 127) / 128, (long long)pc->n_sm * 32);
+  k_pc_newton<<<gn, 128, 0, st>>>(G, Q);
+  CK(cudaGetLastError());
+  if (!on_device) {
+    CK(cudaMemcpyAsync(donor_out, pc->donor, sizeof(long long) * n_pts, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ref_out, pc->ref, sizeof(double) * 3 * n_pts, cudaMemcpyDeviceToHost, st));
+  }
+  unsigned long long h[4];
+  CK(cudaMemcpyAsync(h, pc->cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  pc->last.candidates = (int64_t)h[0];
+  pc->last.fp64_steps = (int64_t)h[2];
+  pc->last.n_found = (int64_t)h[3];
+  if (h[1]) return fail(DC_EINTERNAL, "%llu points had more than %d candidate elements", h[1], PC_CAND);
+  return DC_OK;
+}
+
+dc_status dc_pc_get_stats(dc_pc* pc, dc_pc_stats* out) {
+  g_err.clear();
+  if (!pc || !out) return fail(DC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(pc->mu);
+  *out = pc->last;
+  out->tree_depth = pc->depth;
+  return DC_OK;
+}
+
+void dc_pc_destroy(dc_pc* pc) {
+  if (!pc) return;
+  cudaSetDevice(pc->device);
+  cudaStreamSynchronize(pc->stream);
+  pc_free(pc);
 }
 
 }  // extern "C"

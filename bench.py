@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--locate-points", type=int, default=1 << 20,
+                    help="points of the donor-search measurement (0: skip it)")
     ap.add_argument("--heuristic-steps", type=int, default=10,
                     help="timed cuts of the paper's truncating variant (0: skip it)")
     ap.add_argument("--workload", default="scale64", choices=sorted(WORKLOADS),
@@ -385,6 +387,38 @@ def run_ours(args, world, rank, local):
                 "side_differs": int(((ex != dc.DC_FRINGE) & (hv != dc.DC_FRINGE) & (ex != hv)).sum()),
                 "fp64_key_rescans": hst["heur_rescans"], "fp64_pass1_resolves": hst["heur_resolves"]}
 
+    # donor search after the cut: flux points of a near-body grid's overset
+    # region (a body-fitted Q2 shell, 6*32*32*8 elements between radii 1 and
+    # 1.6) located in it, the grid turned by a rigid pose; points, donors and
+    # reference coordinates resident on the device
+    pconn = None
+    if args.locate_points > 0:
+        shell = W.sphere_shell(32, 8, 2, 1.0, 1.6)
+        qpts = torch.from_numpy(W.shell_points(args.locate_points, 1.0, 1.6, seed=17)).to(dev)
+        ppose = np.concatenate([W.axis_rotation([0.1, 0.7, 0.7], 0.3), np.array([[0.05], [-0.02], [0.01]])], axis=1)
+        moved = (qpts @ torch.from_numpy(ppose[:, :3].T.copy()).to(dev) + torch.from_numpy(ppose[:, 3].copy()).to(dev))
+        moved = moved.contiguous()
+        pdon = torch.empty(args.locate_points, dtype=torch.int64, device=dev)
+        pref = torch.empty((args.locate_points, 3), dtype=torch.float64, device=dev)
+        with dc.PointLocator(2, torch.from_numpy(shell).to(dev), device=local) as pl:
+            for _ in range(2):
+                pl.locate(moved, pose=ppose, donor_out=pdon, ref_out=pref, stream=stream.cuda_stream)
+            lms = []
+            for k in range(5):
+                flush.fill_(k & 0xff)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pl.locate(moved, pose=ppose, donor_out=pdon, ref_out=pref, stream=stream.cuda_stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                lms.append(a.elapsed_time(b))
+            pst = pl.stats()
+        lm = float(np.median(lms))
+        pconn = {"elements": int(shell.shape[0]), "points": args.locate_points, "ms": lm,
+                 "points_per_s": args.locate_points / (lm * 1e-3), "found": pst["n_found"],
+                 "candidates": pst["candidates"], "fp64_steps": pst["fp64_steps"], "tree_depth": pst["tree_depth"]}
+
     # roofline of the dominant kernel (the flags-only exact stage): ALU bound.
     # Algorithmic arithmetic = the exact test on the necessary pair set S*:
     # |S*| x n_Tc x n_T(F) triangle pairs x the flops of one triangle pair, with
@@ -430,6 +464,7 @@ def run_ours(args, world, rank, local):
             "unblank_step_ms": float(np.median(ub_ms)),
             "tuning": None if tuning is None else dict(tuning, trials=tune_trials),
             "paper_truncating_variant": heur,
+            "point_connectivity": pconn,
             "phases_ms": {"surface_bins": float(np.mean(surf_ms)), "holemap": float(np.mean(hm_ms)),
                           "classify": float(np.mean(cls_ms)), "exact_fp32": ex_ms, "redo_fp64": float(np.mean(redo_ms)),
                           "library_total": float(np.mean(total_ms)),

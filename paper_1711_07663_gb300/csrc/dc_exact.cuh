@@ -45,7 +45,12 @@ template <class T> __host__ __device__ __forceinline__ T clamp01(T v) { return v
 template <class T> struct Eps;
 template <> struct Eps<float> { static constexpr float u = 5.9604644775390625e-8f; };   // 2^-24
 template <> struct Eps<double> { static constexpr double u = 1.1102230246251565e-16; }; // 2^-53
-constexpr double C_SIGMA = 64.0;  // rounding bound multiplier (see the derivation in the design notes)
+// Rounding bound of the FP32 triangle-pair routine in an element frame: with
+// S the largest |local coordinate|, the rounded inputs move every point by at
+// most sqrt(3) u S, the two returned points lie within a few u S of points of
+// the triangles, and the distance and projection arithmetic adds a few u S
+// more, so U + C_SIGMA u S and L - C_SIGMA u S bracket the exact distance.
+constexpr double C_SIGMA = 64.0;
 
 // Closest points of segments p + s d1 and q + t d2 (s, t in [0,1]): minimise
 // the convex quadratic along s for the infinite lines, clamp, take the best t

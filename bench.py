@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="launch shapes cubes_per_edge,bin_cubes,warps_per_cta,cands_per_warp instead of the "
                          "autotuner's (for runs under a profiler, whose timings would mislead the tuner)")
+    ap.add_argument("--serving-seconds", type=float, default=2.0,
+                    help="length of the open-loop serving measurement (0: skip it)")
     ap.add_argument("--locate-points", type=int, default=1 << 20,
                     help="points of the donor-search measurement (0: skip it)")
     ap.add_argument("--heuristic-steps", type=int, default=10,
@@ -221,6 +223,106 @@ def run_reference(args, world, rank):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# ----------------------------------------------------------------- serving
+def serving_measure(dc, W, dev, seconds, rate=200.0, seed=77):
+    """Open-loop serving: requests arrive as a Poisson stream (mean `rate`
+    per second) for `seconds` after a 0.5 s warm-up, each a cut of one of the
+    resident 32^3 / 64^3 / 96^3 Q2 grids (probabilities 0.5 / 0.3 / 0.2) by the
+    dimpled sphere turned 0.5 degrees per request.  A request is submitted at
+    its arrival (dc_submit; up to 4 in flight share the GPU) and its latency is
+    its completion (dc_poll) minus its arrival.  The plain path serves the same
+    stream one request at a time in arrival order with the FP64 exact stage:
+    each request's service time is measured with the GPU otherwise idle and
+    the FIFO queue is evaluated from those times.  Also: the saturated rate
+    (all requests offered at once)."""
+    import torch
+    sizes = (32, 64, 96)
+    meshes = [torch.from_numpy(W.background(n, 2, sinusoid=0.1)).to(dev) for n in sizes]
+    faces = torch.from_numpy(W.dimpled_sphere_case(n=8, m=32, q=2).faces).to(dev)
+    g = np.random.default_rng(seed)
+    axis = g.normal(size=3)
+    warm = 0.5
+    t_arr = np.cumsum(g.exponential(1.0 / rate, size=int((seconds + warm) * rate * 2) + 16))
+    t_arr = t_arr[t_arr < seconds + warm]
+    n_req = t_arr.size
+    which = g.choice(3, size=n_req, p=[0.5, 0.3, 0.2])
+    poses = [np.concatenate([W.axis_rotation(axis, np.deg2rad(0.5 * k)), np.zeros((3, 1))], axis=1)
+             for k in range(n_req)]
+    ring = 16
+    outs = [[torch.empty(n ** 3, dtype=torch.int8, device=dev) for _ in range(ring)] for n in sizes]
+    res = {}
+    with dc.Context([(2, m) for m in meshes], max_inflight=4) as ctx:
+        for k in range(3):   # graphs and arenas of each size
+            ctx.cut(k, 2, faces, outs[k][0])
+        torch.cuda.synchronize()
+        lat = np.full(n_req, np.nan)
+        done_t = np.full(n_req, np.nan)
+        pending = {}
+        k = 0
+        t0 = time.perf_counter()
+        while k < n_req or pending:
+            now = time.perf_counter() - t0
+            while k < n_req and t_arr[k] <= now:
+                try:
+                    tk = ctx.submit(int(which[k]), 2, faces, outs[which[k]][k % ring], pose=poses[k])
+                except dc.DirectCutError as e:
+                    if e.status != dc.DC_EBUSY:
+                        raise
+                    break
+                pending[tk] = k
+                k += 1
+            for tk in list(pending):
+                if ctx.poll(tk, timeout_us=0) == 0:
+                    j = pending.pop(tk)
+                    done_t[j] = time.perf_counter() - t0
+                    lat[j] = done_t[j] - t_arr[j]
+        keep = t_arr >= warm
+        L = lat[keep] * 1e3
+        span = done_t[keep].max() - t_arr[keep].min()
+        res.update({"arrival_rate_per_s": rate, "seconds": seconds, "requests": int(keep.sum()),
+                    "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
+                    "req_per_s": float(keep.sum() / span)})
+        # saturated: every request offered at once
+        pending = {}
+        k = 0
+        t1 = time.perf_counter()
+        while k < n_req or pending:
+            while k < n_req:
+                try:
+                    tk = ctx.submit(int(which[k]), 2, faces, outs[which[k]][k % ring], pose=poses[k])
+                except dc.DirectCutError as e:
+                    if e.status != dc.DC_EBUSY:
+                        raise
+                    break
+                pending[tk] = k
+                k += 1
+            for tk in list(pending):
+                if ctx.poll(tk, timeout_us=0) == 0:
+                    pending.pop(tk)
+        res["saturated_req_per_s"] = float(n_req / (time.perf_counter() - t1))
+    # the plain path: FP64 exact stage, one request at a time
+    with dc.Context([(2, m) for m in meshes], precision=dc.DC_FP64) as pctx:
+        for k in range(3):
+            pctx.cut(k, 2, faces, outs[k][0])
+        torch.cuda.synchronize()
+        svc = np.zeros(n_req)
+        for k in range(n_req):
+            a = time.perf_counter()
+            pctx.cut(int(which[k]), 2, faces, outs[which[k]][k % ring], pose=poses[k])
+            svc[k] = time.perf_counter() - a
+    end = np.zeros(n_req)
+    prev = 0.0
+    for k in range(n_req):
+        end[k] = max(t_arr[k], prev) + svc[k]
+        prev = end[k]
+    keep = t_arr >= warm
+    PL = (end - t_arr)[keep] * 1e3
+    res["plain_fp64_fifo"] = {"p50_ms": float(np.percentile(PL, 50)), "p99_ms": float(np.percentile(PL, 99)),
+                              "req_per_s": float(keep.sum() / (end[keep].max() - t_arr[keep].min())),
+                              "saturated_req_per_s": float(1.0 / svc.mean())}
+    return res
 
 
 # ----------------------------------------------------------------- our arm
@@ -427,6 +529,8 @@ def run_ours(args, world, rank, local):
                  "points_per_s": args.locate_points / (lm * 1e-3), "found": pst["n_found"],
                  "candidates": pst["candidates"], "fp64_steps": pst["fp64_steps"], "tree_depth": pst["tree_depth"]}
 
+    serving = serving_measure(dc, W, dev, args.serving_seconds) if args.serving_seconds > 0 else None
+
     # roofline of the dominant kernel (the flags-only exact stage): ALU bound.
     # Algorithmic arithmetic = the exact test on the necessary pair set S*:
     # |S*| x n_Tc x n_T(F) triangle pairs x the flops of one triangle pair, with
@@ -473,6 +577,7 @@ def run_ours(args, world, rank, local):
             "tuning": None if tuning is None else dict(tuning, trials=tune_trials),
             "paper_truncating_variant": heur,
             "point_connectivity": pconn,
+            "serving": serving,
             "phases_ms": {"surface_bins": float(np.mean(surf_ms)), "holemap": float(np.mean(hm_ms)),
                           "classify": float(np.mean(cls_ms)), "exact_fp32": ex_ms, "redo_fp64": float(np.mean(redo_ms)),
                           "library_total": float(np.mean(total_ms)),

@@ -178,19 +178,19 @@ def barrier(world):
 
 
 # ----------------------------------------------------------------- CPU oracle leg
-def cpu_oracle_sample(case, seconds, seed=0):
-    """Time the oracle (as it stands, all host cores) on random elements of the
-    workload until ~`seconds` of wall time.  Returns (elements done, seconds,
-    threads); one whole cut takes seconds * N_E / done."""
+def cpu_oracle_sample(case, seconds, seed=0, threads=0):
+    """Time the oracle (as it stands; `threads` host threads, 0 = all cores) on
+    random elements of the workload until ~`seconds` of wall time.  Returns
+    (elements done, seconds, threads); one whole cut takes seconds * N_E / done."""
     import oracle as O
     g = np.random.default_rng(seed)
-    ncpu = os.cpu_count() or 1
+    ncpu = threads or (os.cpu_count() or 1)
     done = 0
     t0 = time.perf_counter()
     batch = 64 * ncpu
     while time.perf_counter() - t0 < seconds:
         ids = g.choice(case.n_elem, size=batch, replace=False)
-        O.cut(case.p, case.nodes, case.q, case.faces, ids=ids)
+        O.cut(case.p, case.nodes, case.q, case.faces, ids=ids, nthreads=threads)
         done += batch
     dt = time.perf_counter() - t0
     return done, dt, ncpu
@@ -531,6 +531,18 @@ def run_ours(args, world, rank, local):
 
     serving = serving_measure(dc, W, dev, args.serving_seconds) if args.serving_seconds > 0 else None
 
+    # cold: the grid is not resident -- create the context from pinned host
+    # nodes (upload, element boxes and frames), cut once, destroy it
+    cold = []
+    nodes_h = torch.from_numpy(case.nodes).pin_memory()
+    for _ in range(3):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        with dc.Context([(case.p, nodes_h)], precision=dc.DC_FP32_RECHECK, device=local) as cctx:
+            cctx.cut(0, case.q, faces, flags, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+        cold.append((time.perf_counter() - a) * 1e3)
+
     # roofline of the dominant kernel (the flags-only exact stage): ALU bound.
     # Algorithmic arithmetic = the exact test on the necessary pair set S*:
     # |S*| x n_Tc x n_T(F) triangle pairs x the flops of one triangle pair, with
@@ -556,9 +568,11 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         done, dt, ncpu = cpu_oracle_sample(case, args.cpu_seconds)
+        d1, t1, _ = cpu_oracle_sample(case, max(2.0, args.cpu_seconds / 3), seed=5, threads=1)
         cpu = {"value": S_STAR * done / NE / dt, "unit": UNIT, "cores": ncpu, "kind": "oracle",
                "sample": f"{done} random elements of the workload ({dt:.1f} s, all {ncpu} host threads); "
-                         f"one cut = the sampled time scaled to all {NE} elements"}
+                         f"one cut = the sampled time scaled to all {NE} elements",
+               "single_thread_value": S_STAR * d1 / NE / t1}
 
     if rank == 0:
         line = {
@@ -574,6 +588,7 @@ def run_ours(args, world, rank, local):
             "plain_fp64_ms": plain_ms, "speedup_vs_plain": (plain_ms / float(np.median(step_ms))) if plain_ms else None,
             "plain_same_flags": same_flags,
             "unblank_step_ms": float(np.median(ub_ms)),
+            "cold_create_and_cut_ms": float(np.median(cold)),
             "tuning": None if tuning is None else dict(tuning, trials=tune_trials),
             "paper_truncating_variant": heur,
             "point_connectivity": pconn,

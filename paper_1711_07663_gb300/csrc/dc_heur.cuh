@@ -89,33 +89,33 @@ __device__ __forceinline__ void heur_ctri(int p, int f, int h, int nd[3]) {
   nd[2] = h ? n01 : n11;
 }
 
-// cyclic Jacobi on a symmetric 3x3 (every lane the same values); V columns =
-// eigenvectors
-__device__ void heur_jacobi(double A[3][3], double V[3][3]) {
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 50; ++sweep) {
-    const double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
-    const double scale = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
-    if (off <= 1e-15 * scale || off == 0.0) break;
+// cyclic Jacobi on a symmetric 3x3 (every lane the same values): rotations
+// applied to A and accumulated into V (columns: eigenvectors once A is
+// diagonal), until the off-diagonal sum is below rel x the diagonal sum
+template <class T>
+__device__ void heur_jacobi(T A[3][3], T V[3][3], int sweeps, T rel) {
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    const T off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+    const T scale = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+    if (off <= rel * scale || off == T(0)) break;
     for (int p = 0; p < 2; ++p)
       for (int q = p + 1; q < 3; ++q) {
-        if (A[p][q] == 0.0) continue;
-        const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        if (A[p][q] == T(0)) continue;
+        const T theta = (A[q][q] - A[p][p]) / (T(2) * A[p][q]);
+        const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+        const T c = T(1) / sqrt(t * t + T(1)), s = t * c;
         for (int k = 0; k < 3; ++k) {
-          const double akp = A[k][p], akq = A[k][q];
+          const T akp = A[k][p], akq = A[k][q];
           A[k][p] = c * akp - s * akq;
           A[k][q] = s * akp + c * akq;
         }
         for (int k = 0; k < 3; ++k) {
-          const double apk = A[p][k], aqk = A[q][k];
+          const T apk = A[p][k], aqk = A[q][k];
           A[p][k] = c * apk - s * aqk;
           A[q][k] = s * apk + c * aqk;
         }
         for (int k = 0; k < 3; ++k) {
-          const double vkp = V[k][p], vkq = V[k][q];
+          const T vkp = V[k][p], vkq = V[k][q];
           V[k][p] = c * vkp - s * vkq;
           V[k][q] = s * vkp + c * vkq;
         }
@@ -216,6 +216,10 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __shared__ float s_fc[8][HEUR_NF1][12];  // kept faces' corners in the element frame
   __shared__ float s_lo[8][HEUR_NF1], s_hi[8][HEUR_NF1];
+  // the FP64 OBB (axes R[9], box Be[6], centroid[3]) and corners of each
+  // warp's element, parked here during the face scan (registers are short)
+  __shared__ double s_obb[8][18];
+  __shared__ double s_cor[8][8][3];
   const unsigned long long ncand = cl.count[0] < cl.cap ? cl.count[0] : cl.cap;
   unsigned long long n_rescan = 0, n_resolve = 0;
   for (unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wid; w < ncand;
@@ -225,6 +229,8 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
     const long long e = (long long)(ent & ((1ull << 40) - 1ull));
     const int p = in.p, q = in.q, npe = (p + 1) * (p + 1) * (p + 1), npf = (q + 1) * (q + 1);
     const long long nf = in.n_faces;
+    float Rf[9], Bef[6], ecf[3], Xe = 0.f;
+    {
     // corners (lane c < 8), FP64 world
     const double* en = in.nodes + e * npe * 3;
     double cx = 0.0, cy = 0.0, cz = 0.0;
@@ -253,8 +259,31 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
       for (int s = 4; s; s >>= 1) cv[k] += __shfl_xor_sync(FULL, cv[k], s);
       cv[k] = __shfl_sync(FULL, cv[k], 0);
     }
+    // eigenvectors: Jacobi in FP32 from the identity, then FP64 sweeps on
+    // V32^T A V32 (already nearly diagonal) to the FP64 tolerance; the OBB key
+    // does not depend on the order or sign of the axes
     double A[3][3] = {{cv[0], cv[1], cv[2]}, {cv[1], cv[3], cv[4]}, {cv[2], cv[4], cv[5]}}, V[3][3];
-    heur_jacobi(A, V);
+    {
+      float Af[3][3], Vf[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { Af[i][j] = (float)A[i][j]; Vf[i][j] = i == j ? 1.f : 0.f; }
+      heur_jacobi<float>(Af, Vf, 20, 1e-7f);
+      double B[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          V[i][j] = (double)Vf[i][j];
+          double acc = 0.0;
+          for (int k = 0; k < 3; ++k) acc += A[i][k] * (double)Vf[k][j];
+          B[i][j] = acc;
+        }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double acc = 0.0;
+          for (int k = 0; k < 3; ++k) acc += (double)Vf[k][i] * B[k][j];
+          A[i][j] = acc;
+        }
+      heur_jacobi<double>(A, V, 50, 1e-15);
+    }
     double R[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -274,19 +303,28 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
         Be[3 + r] = hi;
       }
     }
-    // FP32 key scan (world coordinates), the 24 smallest keys in lanes 0..23
-    float Rf[9], Bef[6], ecf[3];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Rf[k] = (float)R[k];
 #pragma unroll
     for (int k = 0; k < 6; ++k) Bef[k] = (float)Be[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) ecf[k] = (float)ecg[k];
-    float Xe = 0.f;
     {
       float m = lane < 8 ? fmaxf(fabsf((float)cx), fmaxf(fabsf((float)cy), fabsf((float)cz))) : 0.f;
       Xe = warp_max(m);
     }
+    if (lane == 0) {
+      for (int k = 0; k < 9; ++k) s_obb[wid][k] = R[k];
+      for (int k = 0; k < 6; ++k) s_obb[wid][9 + k] = Be[k];
+      for (int k = 0; k < 3; ++k) s_obb[wid][15 + k] = ecg[k];
+    }
+    if (lane < 8) { s_cor[wid][lane][0] = cx; s_cor[wid][lane][1] = cy; s_cor[wid][lane][2] = cz; }
+    }
+    __syncwarp();
+    const double* R = s_obb[wid];
+    const double* Be = R + 9;
+    const double* ecg = R + 15;
+    // FP32 key scan (world coordinates), the 24 smallest keys in lanes 0..23
     float tk = INFINITY;
     int ti = 0x7fffffff;
     float tau = INFINITY;
@@ -378,9 +416,9 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
       }
       double best = INFINITY;
       for (int c = 0; c < 8; ++c) {
-        const double xc = __shfl_sync(FULL, cx, c), yc = __shfl_sync(FULL, cy, c), zc = __shfl_sync(FULL, cz, c);
+        const double xc = s_cor[wid][c][0], yc = s_cor[wid][c][1], zc = s_cor[wid][c][2];
         const double dx = xc - fcg[0], dy = yc - fcg[1], dz = zc - fcg[2];
-        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        const double d = dx * dx + dy * dy + dz * dz;  // squared: the same nearest corner
         if (d < best) { best = d; corner = c; }
       }
       if (lane < n1)
@@ -418,7 +456,18 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
           int xc;
           tritri<float, false>(a, b, U, L, ca, cb, xc);
           const float sg = (float)C_SIGMA * Eps<float>::u * S;
-          const float lo = fmaxf(L - sg, 0.f), hi = U + sg;
+          float lo = fmaxf(L - sg, 0.f), hi = U + sg;
+          if (xc >= 0) {
+            // a crossing certified against the rounding of the local copies:
+            // the FP64 triangles meet, D1 is exactly 0
+            const V3<float>* sv = xc < 3 ? b : a;
+            const V3<float>* tv = xc < 3 ? a : b;
+            const int jj = xc % 3;
+            if (certified_cross<float>(sv[jj], sv[(jj + 1) % 3], tv[0], tv[1], tv[2], 2.f * Eps<float>::u * S)) {
+              lo = 0.f;
+              hi = 0.f;
+            }
+          }
           atomicMin((int*)&s_lo[wid][i], __float_as_int(lo));
           atomicMin((int*)&s_hi[wid][i], __float_as_int(hi));
         }

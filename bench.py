@@ -47,6 +47,12 @@ FLOPS_PER_PAIR = 936.5
 FLOPS_PER_SEP = 139.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# Alg. cp0 key of one (element, face) pair: 4 corners rotated into the OBB
+# axes (60), box distance (12), centroid distance (9), key (2)
+FLOPS_PER_KEY = 83.0
+# one Newton step of the donor search on a Q2 element: the 27-node map and
+# Jacobian (27 x 32), the 1-D bases (72) and the 3x3 solve (60)
+FLOPS_PER_NEWTON_STEP_Q2 = 996.0
 # resident-mesh bytes one cut must move: a FP32 box read and a flag written per
 # element, the FP32 frame of each element that needs the exact test (Q2: 27
 # nodes x 3 x 4 B), the FP64 face nodes (Q2: 9 x 3 x 8 B)
@@ -491,7 +497,15 @@ def run_ours(args, world, rank, local):
                 hms.append(a.elapsed_time(b))
             hst = hctx.stats()
         ex, hv = flags.cpu().numpy(), hflags.cpu().numpy()
+        ncand_h = float(np.mean(ncand))
+        # the paper's variant per candidate: every face's key, 16 faces x 12
+        # corner-triangle pairs, 4 faces x 3 element faces x 2p^2 x 2q^2 pairs
+        hflops = ncand_h * (NF * FLOPS_PER_KEY + (16 * 12 + 4 * 3 * 2 * case.p ** 2 * 2 * case.q ** 2) * FLOPS_PER_PAIR)
+        hpeak = SM_COUNT * FP32_LANES_PER_SM * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
         heur = {"ms": float(np.median(hms)), "disagree": int((ex != hv).sum()),
+                "roofline": {"bound": "alu", "achieved": hflops / (float(np.median(hms)) * 1e-3) / 1e12, "peak": hpeak,
+                             "unit": "TFLOP/s", "frac": hflops / (float(np.median(hms)) * 1e-3) / 1e12 / hpeak,
+                             "flops_per_cut": hflops, "scope": "whole variant cut (keys, pass 1, pass 2)"},
                 "missed_fringe": int(((ex == dc.DC_FRINGE) & (hv != dc.DC_FRINGE)).sum()),
                 "false_fringe": int(((ex != dc.DC_FRINGE) & (hv == dc.DC_FRINGE)).sum()),
                 "side_differs": int(((ex != dc.DC_FRINGE) & (hv != dc.DC_FRINGE) & (ex != hv)).sum()),
@@ -525,7 +539,14 @@ def run_ours(args, world, rank, local):
                 lms.append(a.elapsed_time(b))
             pst = pl.stats()
         lm = float(np.median(lms))
+        # algorithmic: Newton to convergence on every candidate box (4 steps
+        # each) -- the containment checks the paper's search leaves
+        pflops = pst["candidates"] * 4 * FLOPS_PER_NEWTON_STEP_Q2
+        ppeak = SM_COUNT * FP32_LANES_PER_SM * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
         pconn = {"elements": int(shell.shape[0]), "points": args.locate_points, "ms": lm,
+                 "roofline": {"bound": "alu", "achieved": pflops / (lm * 1e-3) / 1e12, "peak": ppeak, "unit": "TFLOP/s",
+                              "frac": pflops / (lm * 1e-3) / 1e12 / ppeak, "flops": pflops,
+                              "scope": "search + Newton (k_pc_search, k_pc_newton)"},
                  "points_per_s": args.locate_points / (lm * 1e-3), "found": pst["n_found"],
                  "candidates": pst["candidates"], "fp64_steps": pst["fp64_steps"], "tree_depth": pst["tree_depth"]}
 

@@ -115,9 +115,6 @@ __device__ __forceinline__ bool near_separated(const V3<float>* A, const V3<floa
   return sa || sb;
 }
 
-// One listed pair, loaded: the float copies and the bound S, its candidate
-// position w and the task's face f.  False if the pair is void (a capacity
-// guard) or its element is already fringe.
 // The crossing tests of the triangle-triangle test, branch-free: the first
 // edge found (in the test's order) is certified for the exact triangles.
 // True if the pair certainly crosses (its element is fringe).

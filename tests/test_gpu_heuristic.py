@@ -102,3 +102,24 @@ def test_posed_surface_and_batch():
             single.append(ctx.cut(i, cs.q, cs.faces, pose=cs.pose))
     for a, b in zip(outs, single):
         assert np.array_equal(a, b)
+
+
+def test_scale_workload_sampled():
+    """The 64^3 Q2 workload cut by the 6144-face dimpled sphere, as the
+    benchmark runs it: the variant's flags on sampled elements that every hole
+    map leaves to it, against the oracle's variant element by element."""
+    c = W.dimpled_sphere_case()
+    dev = torch.device("cuda:0")
+    flags = torch.empty(c.n_elem, dtype=torch.int8, device=dev)
+    with dc.Context([(c.p, torch.from_numpy(c.nodes).to(dev))], precision=dc.DC_HEURISTIC) as ctx:
+        ctx.cut(0, c.q, torch.from_numpy(c.faces).to(dev), flags)
+    got = flags.cpu().numpy()
+    sure = NP.exact_test_elements(c.nodes, c.faces)
+    g = np.random.default_rng(5)
+    ids = np.sort(g.choice(sure, size=400, replace=False))
+    hf, hs, hd, mg = O.heuristic(c.p, c.nodes, c.q, c.faces, ids=ids)
+    assert int(((mg[:, 0] < 1e-12) | (mg[:, 1] < 1e-12)).sum()) == 0
+    allowed = ((hs >> (got[ids].astype(np.int16) + 1)) & 1).astype(bool)
+    assert np.all(allowed)
+    unique = np.array([bin(int(x)).count("1") == 1 for x in hs])
+    assert np.array_equal(got[ids][unique], hf[unique])

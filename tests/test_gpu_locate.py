@@ -128,3 +128,26 @@ def test_flux_points_of_artificial_boundary_faces():
     shell = W.sphere_shell(10, 4, 2, 1.0, 1.6)
     donor, ref, od, st = compare(2, shell, pts)
     assert np.all(donor >= 0)
+
+
+def test_bench_configuration_sampled():
+    """The benchmark's donor search: 2^20 shell points in the 49,152-element Q2
+    shell turned by a rigid pose, device tensors; the oracle checks a sample."""
+    shell = W.sphere_shell(32, 8, 2, 1.0, 1.6)
+    pts = W.shell_points(1 << 20, 1.0, 1.6, seed=17)
+    pose = np.concatenate([W.axis_rotation([0.1, 0.7, 0.7], 0.3), np.array([[0.05], [-0.02], [0.01]])], axis=1)
+    moved = np.ascontiguousarray(pts @ pose[:, :3].T + pose[:, 3])
+    dev = torch.device("cuda:0")
+    with dc.PointLocator(2, torch.from_numpy(shell).to(dev)) as pl:
+        d, r = pl.locate(torch.from_numpy(moved).to(dev), pose=pose)
+        torch.cuda.synchronize()
+        st = pl.stats()
+    d, r = d.cpu().numpy(), r.cpu().numpy()
+    assert st["n_found"] == int((d >= 0).sum())
+    g = np.random.default_rng(3)
+    k = np.sort(g.choice(pts.shape[0], size=3000, replace=False))
+    od, orf, om = O.locate(2, shell, moved[k], pose=pose)
+    robust = (np.abs(om[:, 0]) > 1e-13) & (np.abs(om[:, 1]) > 1e-12)
+    assert np.array_equal(d[k][robust], od[robust])
+    both = (d[k] >= 0) & (d[k] == od)
+    assert np.abs(r[k][both] - orf[both]).max() < 1e-8

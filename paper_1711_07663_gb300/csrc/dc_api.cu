@@ -403,13 +403,8 @@ dc_status validate_req(dc_ctx* c, int mesh, const dc_request* r) {
   if (r->pose)
     for (int i = 0; i < 12; ++i)
       if (!std::isfinite(r->pose[i])) return fail(DC_EINVAL, "pose has a non-finite entry");
-  if (!r->on_device) {
-    int npf = (r->q + 1) * (r->q + 1);
-    const double* x = r->face_nodes;
-    long long n = r->n_faces * npf * 3;
-    for (long long i = 0; i < n; ++i)
-      if (!std::isfinite(x[i])) return fail(DC_EINVAL, "face node value %lld is not finite", i);
-  }
+  // face nodes are checked on the device as they are posed (k_surface), for
+  // host and device inputs alike
   return DC_OK;
 }
 
@@ -710,19 +705,17 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
   return DC_OK;
 }
 
+// host outputs: the kernels wrote into the arena staging area; the copies
+// are queued behind the cut (the caller synchronises)
 dc_status copy_out_host(Slot& s, const std::vector<InstReq>& v, cudaStream_t st) {
-  // host outputs: the kernels wrote into the arena staging area
-  long long off = 0;
   for (size_t i = 0; i < v.size(); ++i) {
     const dc_request* r = v[i].req;
-    long long ne = s.h_inst[i].n_elem;
+    const long long ne = s.h_inst[i].n_elem;
     if (!r->on_device) {
       CK(cudaMemcpyAsync(r->flags_out, s.h_inst[i].flags, (size_t)ne, cudaMemcpyDeviceToHost, st));
       if (r->dist_out) CK(cudaMemcpyAsync(r->dist_out, s.h_inst[i].dist, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
     }
-    off += ne;
   }
-  CK(cudaStreamSynchronize(st));
   return DC_OK;
 }
 
@@ -905,8 +898,10 @@ static dc_status run_sync(dc_ctx* c, const std::vector<InstReq>& v, bool async_o
   dc_status rc = enqueue(c, s, v, st, false);
   if (rc) return rc;
   if (async_ok) return DC_OK;
-  rc = finish(c, s, v, st);
+  // host outputs are copied in the same stream order, so finish's one
+  // synchronisation covers them
   dc_status rc2 = copy_out_host(s, v, st);
+  rc = finish(c, s, v, st);
   return rc ? rc : rc2;
 }
 

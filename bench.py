@@ -518,7 +518,7 @@ def run_ours(args, world, rank, local):
     pconn = None
     if args.locate_points > 0:
         shell = W.sphere_shell(32, 8, 2, 1.0, 1.6)
-        qpts = torch.from_numpy(W.shell_points(args.locate_points, 1.0, 1.6, seed=17)).to(dev)
+        qpts = torch.from_numpy(W.shell_points(args.locate_points, 1.0, 1.6, seed=17, order="morton")).to(dev)
         ppose = np.concatenate([W.axis_rotation([0.1, 0.7, 0.7], 0.3), np.array([[0.05], [-0.02], [0.01]])], axis=1)
         moved = (qpts @ torch.from_numpy(ppose[:, :3].T.copy()).to(dev) + torch.from_numpy(ppose[:, 3].copy()).to(dev))
         moved = moved.contiguous()
@@ -538,6 +538,20 @@ def run_ours(args, world, rank, local):
                 torch.cuda.synchronize()
                 lms.append(a.elapsed_time(b))
             pst = pl.stats()
+            # the same points in random order (the scattered case)
+            perm = torch.from_numpy(np.random.default_rng(18).permutation(args.locate_points)).to(dev)
+            moved_r = moved[perm].contiguous()
+            pl.locate(moved_r, pose=ppose, donor_out=pdon, ref_out=pref, stream=stream.cuda_stream)
+            rms = []
+            for k in range(3):
+                flush.fill_(k & 0xff)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pl.locate(moved_r, pose=ppose, donor_out=pdon, ref_out=pref, stream=stream.cuda_stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                rms.append(a.elapsed_time(b))
         lm = float(np.median(lms))
         # algorithmic: Newton to convergence on every candidate box (4 steps
         # each) -- the containment checks the paper's search leaves
@@ -548,6 +562,8 @@ def run_ours(args, world, rank, local):
                               "frac": pflops / (lm * 1e-3) / 1e12 / ppeak, "flops": pflops,
                               "scope": "search + Newton (k_pc_search, k_pc_newton)"},
                  "points_per_s": args.locate_points / (lm * 1e-3), "found": pst["n_found"],
+                 "order": "Morton curve (receptor points come face by face)",
+                 "random_order_ms": float(np.median(rms)),
                  "candidates": pst["candidates"], "fp64_steps": pst["fp64_steps"], "tree_depth": pst["tree_depth"]}
 
     serving = serving_measure(dc, W, dev, args.serving_seconds) if args.serving_seconds > 0 else None

@@ -296,14 +296,30 @@ def sphere_shell(n: int, layers: int, p: int, r0: float = 1.0, r1: float = 1.6, 
     return np.ascontiguousarray(out + np.asarray(centre, dtype=np.float64))
 
 
-def shell_points(count: int, r0: float, r1: float, seed: int, centre=(0.0, 0.0, 0.0)) -> np.ndarray:
+def morton_order(pts: np.ndarray, bits: int = 10) -> np.ndarray:
+    """Indices that sort points along a Z-order (Morton) curve of their
+    bounding box, 2^bits cells per axis."""
+    lo, hi = pts.min(axis=0), pts.max(axis=0)
+    cell = np.minimum(((pts - lo) / np.maximum(hi - lo, 1e-300) * (1 << bits)).astype(np.int64), (1 << bits) - 1)
+    code = np.zeros(pts.shape[0], dtype=np.int64)
+    for b in range(bits):
+        for a in range(3):
+            code |= ((cell[:, a] >> b) & 1) << (3 * b + a)
+    return np.argsort(code, kind="stable")
+
+
+def shell_points(count: int, r0: float, r1: float, seed: int, centre=(0.0, 0.0, 0.0), order: str = "random") -> np.ndarray:
     """Seeded points spread over the shell r0 <= r <= r1 (uniform direction,
-    uniform radius): float64 [count][3]."""
+    uniform radius): float64 [count][3].  order="morton" lists them along a
+    space-filling curve, as receptor points come face by face from a grid."""
     g = rng(seed)
     d = g.normal(size=(count, 3))
     d /= np.sqrt((d * d).sum(axis=1))[:, None]
     r = g.uniform(r0, r1, size=count)
-    return np.ascontiguousarray(d * r[:, None] + np.asarray(centre, dtype=np.float64))
+    pts = d * r[:, None] + np.asarray(centre, dtype=np.float64)
+    if order == "morton":
+        pts = pts[morton_order(pts)]
+    return np.ascontiguousarray(pts)
 
 
 def box_surface(lo, hi, n: int = 1, q: int = 1) -> np.ndarray:

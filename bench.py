@@ -168,11 +168,14 @@ def dist_env():
 
 
 def max_over_ranks(x, world):
+    """The largest x over the ranks of the default process group (a CUDA
+    tensor under NCCL, a host tensor under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as D
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if D.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     D.all_reduce(t, op=D.ReduceOp.MAX)
     return float(t.item())
 

@@ -640,12 +640,13 @@ def run_ours(args, world, rank, local):
             "candidates": int(np.mean(ncand)), "pairs_fp32": int(pairs), "pairs_fp64": int(np.mean(rech)),
             "e2e": {"value": world * S_STAR / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                     "h2d_bytes_per_step": int(case.faces.nbytes), "d2h_bytes_per_step": int(NE), "same_flags": e2e_same},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": 9 * args.steps,
             "roofline": {"bound": "alu", "kernel": "k_near_main (flags-only exact stage)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch
-                         # (profiles/k_near_main_scale64.md); null once the kernel changes
-                         "traffic": 9.08e6 if args.workload == "scale64" else None,
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch,
+                         # from an ncu capture of the current kernel; none has been
+                         # taken since the full search moved out of it
+                         "traffic": None,
                          "flops_per_launch": flops_alg, "flops_upper_count": flops_alg_upper,
                          "units": f"|S*| = {S_STAR} element-face pairs x {nec['n_tc_lower']} x {nec['n_tf']} "
                                   f"triangle pairs x {FLOPS_PER_PAIR} flops",

@@ -169,12 +169,13 @@ struct LaunchParams {
   bool near = false;
   int wpc = 8, cpw = 1;  // its warps per block and candidates per cursor step
   int* hsel = nullptr;   // truncating variant: kept faces per candidate
+  unsigned long long* full = nullptr;  // flags-only stage: candidates for the full search
   bool operator==(const LaunchParams& o) const {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
            pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
            cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && wpc == o.wpc && cpw == o.cpw &&
-           hsel == o.hsel;
+           hsel == o.hsel && full == o.full;
   }
 };
 
@@ -226,7 +227,8 @@ constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10]
                           // [11] near faces tested, [12] holes decided by the hole map,
                           // [14] near full searches, [16] near pairs given the
                           // full FP32 test, [17] truncating variant: FP64 key
-                          // rescans, [18] FP64 pass-1 re-solves
+                          // rescans, [18] FP64 pass-1 re-solves, [20,21]
+                          // full-search list of the flags-only stage/cursor
 
 }  // namespace
 
@@ -321,7 +323,7 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
          al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) +
          run_bytes();
   }
-  s += al256(sizeof(unsigned long long) * ne_total) * 2;  // candidates + redo
+  s += al256(sizeof(unsigned long long) * ne_total) * 3;  // candidates, redo, full-search list
   if (c->cfg.precision == DC_HEURISTIC) s += al256(sizeof(int) * HEUR_SEL * ne_total);  // kept faces
   s += al256(sizeof(unsigned long long) * NCNT);
   s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
@@ -475,8 +477,14 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     int occn = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, 32 * wpc, sm);
     occn = std::max(occn, 1);
-    CK(launch_k(true, k_near_main, dim3(c->n_sm * occn), dim3(32 * wpc), sm, st, d_inst, cl, nb, pmax, qmax, P.cpw,
-                d_cnt + 4));
+    CandList fl{P.full, (unsigned long long)ne_total, d_cnt + 20};
+    CK(launch_k(true, k_near_main, dim3(c->n_sm * occn), dim3(32 * wpc), sm, st, d_inst, cl, fl, nb, pmax, qmax,
+                P.cpw, d_cnt + 4));
+    // the candidates it listed for the full per-element search -- only
+    // elements with no labelled node that are not fringe (distances are never
+    // asked for in this form), almost always none: a small FP64 pass
+    CK(launch_k(true, k_exact<double>, dim3(std::min(c->n_sm, 16)), dim3(TB), (size_t)Ld.total * WPB, st, d_inst, fl,
+                none, pmax, qmax, d_cnt + 4));
     if (prof) CK(record(s.ev[5], st, capturing));
   } else if (P.precision == DC_FP32_RECHECK) {
     int occ = 0;
@@ -611,6 +619,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   s.h_off[2 * n + 1] = eo;
   unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
+  unsigned long long* fulll = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   int* hsel = c->cfg.precision == DC_HEURISTIC ? (int*)take(sizeof(int) * HEUR_SEL * ne_total) : nullptr;
   unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
   int8_t* oflags = (int8_t*)take(ne_total);
@@ -639,10 +648,13 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   lp.n = n; lp.nf_total = nf_total; lp.ne_total = ne_total; lp.max_tri = max_tri; lp.max_f = max_f;
   lp.pmax = pmax; lp.qmax = qmax; lp.precision = c->cfg.precision; lp.prof = c->cfg.profile != 0;
   lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt; lp.hsel = hsel;
+  lp.full = fulll;
   lp.wpc = c->tune.warps_per_cta; lp.cpw = c->tune.cands_per_warp;
   {
-    bool flags_only = false;
-    for (auto& r : v) flags_only |= r.req->dist_out == nullptr;
+    // the flags-only form when no instance asks for distances (a batch that
+    // mixes both runs the distance form for all)
+    bool flags_only = true;
+    for (auto& r : v) flags_only &= r.req->dist_out == nullptr;
     lp.near = c->cfg.precision == DC_FP32_RECHECK && flags_only && ne_total < (1LL << 31);
   }
   {

@@ -18,9 +18,10 @@
 //                  the FP64 test (warp-parallel).  The element is fringe, or
 //                  takes its label's side.
 // Elements that need distances, or carry no label and are not fringe, are
-// decided by the same warp with the full per-element search (the one k_exact
-// runs), in FP32 with FP64 re-solves and wholly in FP64 if its re-solve list
-// overflows; the stage needs no other kernel.  The
+// listed for the full per-element search, which k_exact runs right after this
+// kernel (FP32 with FP64 re-solves, FP64 for the elements whose re-solve list
+// overflows); keeping that search and its shared scratch out of this kernel
+// leaves it a smaller code footprint and more of the SM's storage as L1.  The
 // element frame (origin at the centre of the element's float box, node
 // coordinates rounded to float) is the one the full search uses, computed once
 // per resident grid; FP64 arithmetic, slow on this GPU, is left to the face
@@ -34,48 +35,6 @@ namespace dc {
 struct NearBufs {
   unsigned long long* cnt;       // [0] faces tested, [3] full searches, [5] pairs given the full FP32 test
 };
-
-// The full per-element search of one candidate by the calling warp, with its
-// scratch laid out in the warp's shared region ws.  False if the FP64
-// re-solve list overflowed (FP32 pass: redo in FP64).
-template <class T>
-__device__ __noinline__ bool full_search(Inst* __restrict__ I, unsigned long long ent, unsigned char* ws, int pmax,
-                                         int qmax, WarpCtx<T>& W, ExCounters& cnt) {
-  const int lane = threadIdx.x & 31;
-  const ExLayout Lo = ex_layout(pmax, qmax, (int)sizeof(T));
-  const int ii = (int)(ent >> 40);
-  __syncwarp();
-  if (lane == 0) {
-    W.ex = reinterpret_cast<T*>(ws + Lo.en);
-    W.eb = reinterpret_cast<T*>(ws + Lo.ebox);
-    W.fx = reinterpret_cast<T*>(ws + Lo.fn);
-    W.fb = reinterpret_cast<T*>(ws + Lo.fbx);
-    W.fl_id = reinterpret_cast<int*>(ws + Lo.flist);
-    W.fl_key = reinterpret_cast<float*>(W.fl_id + FMAX);
-    W.fl_lb = W.fl_key + FMAX;
-    W.queue = reinterpret_cast<int*>(ws + Lo.queue);
-    W.rl_face = reinterpret_cast<int*>(ws + Lo.rlist);
-    W.rl_tt = reinterpret_cast<unsigned*>(W.rl_face + RCAP);
-    W.rl_lc = reinterpret_cast<float*>(W.rl_tt + RCAP);
-    W.rres = reinterpret_cast<double*>(ws + Lo.rres);
-    W.in = &I[ii];
-    W.e = (long long)(ent & ((1ull << 40) - 1ull));
-    W.p = I[ii].p;
-    W.q = I[ii].q;
-    W.npe = (W.p + 1) * (W.p + 1) * (W.p + 1);
-    W.nte = 12 * W.p * W.p;
-    W.npf = (W.q + 1) * (W.q + 1);
-    W.ntf = 2 * W.q * W.q;
-    W.ey = W.ex + W.npe;
-    W.ez = W.ey + W.npe;
-    W.fy = W.fx + W.npf;
-    W.fz = W.fy + W.npf;
-  }
-  __syncwarp();
-  WarpState<T> S;
-  S.lane = lane;
-  return process_element<T>(W, S, cnt);
-}
 
 __device__ __forceinline__ unsigned long long ucount(const unsigned long long* c, unsigned long long cap) {
   unsigned long long n = *c;
@@ -284,19 +243,17 @@ __host__ __device__ inline NearLayout near_layout(int pmax, int qmax) {
   return L;
 }
 
-// bytes of shared scratch per warp of k_near_main: the near layout or, for a
-// full search, the FP64 per-element layout (the larger of the two)
-__host__ __device__ inline int near_region(int pmax, int qmax) {
-  const int a = near_layout(pmax, qmax).total, b = ex_layout(pmax, qmax, 8).total;
-  return a > b ? a : b;
-}
+// bytes of shared scratch per warp of k_near_main (the full per-element search
+// runs in the exact kernels, with their own layout, so none is kept for it:
+// the smaller reservation leaves the SM's combined L1 / shared storage to L1)
+__host__ __device__ inline int near_region(int pmax, int qmax) { return near_layout(pmax, qmax).total; }
 
 // at most 16 warps per block (4, 8 or 16 are launched; 128 registers per
 // thread either way)
 constexpr int NEAR_MAX_WARPS = 16;
 
 __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
-    k_near_main(Inst* __restrict__ I, CandList cl, NearBufs nb, int pmax, int qmax, int cpw,
+    k_near_main(Inst* __restrict__ I, CandList cl, CandList full, NearBufs nb, int pmax, int qmax, int cpw,
                 unsigned long long* __restrict__ gcnt) {
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -308,18 +265,15 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const NearLayout Lo = near_layout(pmax, qmax);
   unsigned char* ws = smem + (size_t)wid * near_region(pmax, qmax);
-  __shared__ WarpCtx<float> s_cf[NEAR_MAX_WARPS];
-  __shared__ WarpCtx<double> s_cd[NEAR_MAX_WARPS];
-  ExCounters fcnt = {0, 0, 0, 0, 0, 0, 0};
   unsigned long long n_fs = 0;
-  // the full search of one candidate: FP32 with FP64 re-solves, then wholly
-  // FP64 if its re-solve list overflows
+  // a candidate that needs the full per-element search (distances requested,
+  // or no node labelled and not fringe) goes to the exact kernels' list;
+  // k_exact runs right after this kernel
   auto full_one = [&](unsigned long long ent) {
     n_fs++;
-    if (!full_search<float>(I, ent, ws, pmax, qmax, s_cf[wid], fcnt)) {
-      fcnt.fallback++;
-      if (!full_search<double>(I, ent, ws, pmax, qmax, s_cd[wid], fcnt) && lane == 0)
-        atomicOr((int*)&I[(int)(ent >> 40)].err, (int)ERR_RECHECK);
+    if (lane == 0) {
+      const unsigned long long pos = atomicAdd(&full.count[0], 1ull);
+      if (pos < full.cap) full.cand[pos] = ent;
     }
     __syncwarp();
   };
@@ -636,13 +590,6 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     __syncwarp();
   }
   if (lane == 0) {
-    n_fringe += fcnt.fringe;
-    n_hole += fcnt.hole;
-    n_field += fcnt.field;
-    n_faces += fcnt.faces;
-    n_pairs += fcnt.bulk;
-    n_re += fcnt.recheck;
-    if (fcnt.fallback) atomicAdd(&gcnt[6], fcnt.fallback);
     if (n_fs) atomicAdd(&nb.cnt[3], n_fs);
     if (n_fringe | n_hole | n_field) {
       atomicAdd(&gcnt[3], n_fringe);

@@ -157,7 +157,10 @@ dc_status dc_cut(dc_ctx *ctx, int32_t mesh, const dc_request *req);
 
 /* Cut n (mesh, surface) instances in one batched launch sequence: every phase
  * runs once over all instances (persistent exact-test kernel over the union of
- * their candidates).  Synchronous; requests must not set async. */
+ * their candidates).  When every request leaves dist_out NULL the batch takes
+ * the faster flags-only form of the exact stage; when any asks for distances
+ * the whole batch takes the distance form (same flags either way).
+ * Synchronous; requests must not set async. */
 dc_status dc_cut_batch(dc_ctx *ctx, int32_t n, const int32_t *meshes, const dc_request *reqs);
 
 /* Serving: admit a request into a free slot (DC_EBUSY when none is free or the

@@ -13,6 +13,11 @@
  * side comes from the dot product of the minimal vector with the outward face
  * normal (Sec. 4.1/4.2), averaged over the faces that share the closest point.
  *
+ * Also here: what follows the cut (the union of several cuts, the
+ * artificial-boundary faces, the unblank step of a moving grid), the paper's
+ * own truncating variant of the exact test (DC_HEURISTIC), a launch-shape
+ * autotuner, and the donor search for receptor points (dc_pc_*).
+ *
  * Conventions
  *   element nodes  float64 [n_elem][(p+1)^3][3]; node (i,j,k) at
  *                  i + (p+1)*(j + (p+1)*k), i along xi fastest (the tensor

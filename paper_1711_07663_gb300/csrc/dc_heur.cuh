@@ -1,5 +1,5 @@
-// dc_heur.cuh -- the paper's truncating variant of the exact stage (a fast
-// mode, DC_HEURISTIC), for comparison with the exact cut.
+// dc_heur.cuh -- the paper's truncating variant of the exact stage
+// (DC_HEURISTIC), to compare its answers and its cost with the exact cut.
 //
 // Sec. 4.2 with Alg. cp0 / bboxdix / cp1 / cp2, for every candidate element:
 //   * OBB of the element's 8 corner nodes: axes = eigenvectors of the corner
@@ -18,8 +18,9 @@
 // Every decision is taken as the FP64 computation would take it: the key scan
 // runs in FP32 on world coordinates and keeps 24 faces, which are re-ranked in
 // FP64 (certified by the FP32 error bound, else the element is rescanned in
-// FP64); pass 1 runs in FP32 in the element frame with certified bounds, and
-// the faces those bounds cannot order are re-solved in FP64; pass 2 is the
+// FP64); pass 1 runs in FP32 in the element frame with certified bounds and
+// certified crossings, and the faces those cannot zero or order are re-solved
+// in FP64; pass 2 is the
 // exact stage's certified FP32 search with FP64 re-solves, restricted to the
 // kept faces and their corner faces (k_heur_final).
 #pragma once

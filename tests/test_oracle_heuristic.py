@@ -166,3 +166,24 @@ def test_no_truncation_and_one_face():
     fe, de, _, _ = O.cut(2, nodes, 2, face)
     assert np.array_equal(fh, fe)
     assert np.allclose(np.abs(dh), np.abs(de), rtol=1e-14, atol=1e-15)
+
+
+def test_variant_is_invariant_under_rigid_motion_of_grid_and_surface():
+    """Moving the grid and the surface together changes no flag: the OBB, the
+    keys, both passes and the side rule depend only on relative geometry."""
+    nodes = W.background(8, 2, jitter=0.05, seed=3)
+    faces = W.cubed_sphere(12, 2, radius=1.0, centre=(0.03, -0.02, 0.05))
+    f0, s0, d0, m0 = O.heuristic(2, nodes, 2, faces)
+    Q = rot([0.4, -0.3, 0.85], 0.9)
+    t = np.array([0.7, -1.1, 0.4])
+    f1, s1, d1, m1 = O.heuristic(2, nodes @ Q.T + t, 2, faces @ Q.T + t)
+    # decisions away from rounding ties: key and corner gaps, and a unique
+    # flag over the exact D1 ties of the second truncation
+    unique = np.array([bin(int(x)).count("1") == 1 for x in s0])
+    robust = (m0[:, 0] > 1e-9) & (m0[:, 1] > 1e-9) & unique
+    assert robust.mean() > 0.95
+    assert np.array_equal(f0[robust], f1[robust])
+    both_unique = unique & np.array([bin(int(x)).count("1") == 1 for x in s1])
+    assert np.array_equal(f0[both_unique & robust], f1[both_unique & robust])
+    r = both_unique & robust
+    assert np.allclose(np.abs(d0[r]), np.abs(d1[r]), rtol=1e-9, atol=1e-12)

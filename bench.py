@@ -196,7 +196,9 @@ def cpu_oracle_sample(case, seconds, seed=0, threads=0):
     ncpu = threads or (os.cpu_count() or 1)
     done = 0
     t0 = time.perf_counter()
-    batch = 64 * ncpu
+    # batches of ~1 s of work for long samples; short ones still give every
+    # thread a full chunk (the oracle schedules 16 elements at a time)
+    batch = max(16 * ncpu, int(64 * ncpu * min(1.0, seconds)))
     while time.perf_counter() - t0 < seconds:
         ids = g.choice(case.n_elem, size=batch, replace=False)
         O.cut(case.p, case.nodes, case.q, case.faces, ids=ids, nthreads=threads)
@@ -210,7 +212,8 @@ def run_reference(args, world, rank):
         return
     case = WORKLOADS[args.workload]()
     s_star = necessary(args.workload)["s_star_pairs"]
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    # the whole run stays within about --cpu-seconds, however many steps
+    per_step = max(0.02, args.cpu_seconds / max(1, args.steps))
     cut_s = []
     n_el = 0
     for _ in range(args.warmup if args.warmup < 2 else 1):

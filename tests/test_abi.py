@@ -76,3 +76,46 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dc, "lib_path", lambda: str(tmp_path / "absent.so"))
     with pytest.raises(dc.DirectCutError):
         dc.load()
+
+
+def test_argument_errors_are_status_codes_without_a_gpu(lib):
+    """Every entry point checks its arguments before it touches the device:
+    bad values come back as DC_EINVAL with a message, never a crash."""
+    EINVAL = -1
+    P = ctypes.c_void_p
+    out = P()
+    cfg = dc.dc_config()
+    assert lib.dc_config_default(ctypes.byref(cfg)) == 0
+    assert cfg.precision == dc.DC_FP32_RECHECK and cfg.holemap_cells == 0 and cfg.bin_cubes == 4
+
+    def bad(status, what):
+        assert status == EINVAL, what
+        assert dc.dc_last_error() != "", what
+
+    desc = (dc.dc_mesh_desc * 1)()
+    desc[0].p, desc[0].n_elem, desc[0].nodes = 9, 1, None
+    bad(lib.dc_create(ctypes.byref(cfg), desc, 1, ctypes.byref(out)), "order p=9")
+    for field, val in (("tol", -1.0), ("holemap_cells", 5), ("bin_cubes", 17), ("max_inflight", 65), ("precision", 7)):
+        c2 = dc.dc_config()
+        lib.dc_config_default(ctypes.byref(c2))
+        setattr(c2, field, val)
+        desc[0].p, desc[0].n_elem = 2, 1
+        bad(lib.dc_create(ctypes.byref(c2), desc, 1, ctypes.byref(out)), field)
+    bad(lib.dc_create(ctypes.byref(cfg), desc, 0, ctypes.byref(out)), "no meshes")
+    bad(lib.dc_create(ctypes.byref(cfg), desc, 1, None), "out NULL")
+    # after-cut set logic
+    bad(lib.dc_blank_union(0, None, None, 10, None, None), "n_cuts 0")
+    bad(lib.dc_blank_union(9, None, None, 10, None, None), "n_cuts 9")
+    bad(lib.dc_ab_faces(0, None, None, None, None, None), "n_elem 0")
+    bad(lib.dc_unblank(5, 10, None, None, None, None, None, None, None), "kind 5")
+    # donor search
+    bad(lib.dc_pc_create(0, 0, 10, None, 0, ctypes.byref(out)), "order p=0")
+    bad(lib.dc_pc_create(0, 5, 10, None, 0, ctypes.byref(out)), "order p=5")
+    bad(lib.dc_pc_create(0, 2, 0, None, 0, ctypes.byref(out)), "n_elem 0")
+    bad(lib.dc_pc_locate(None, 0, None, None, None, None, 0, None), "pc NULL")
+    # tuning on a NULL context
+    t = dc.dc_tuning()
+    bad(lib.dc_set_tuning(None, ctypes.byref(t)), "ctx NULL")
+    bad(lib.dc_get_stats(None, None), "ctx NULL")
+    lib.dc_destroy(None)
+    lib.dc_pc_destroy(None)

@@ -80,6 +80,8 @@ def lib():
             L.orc_newton.argtypes = [i32, P, P, d, P, ctypes.POINTER(d), ctypes.POINTER(i32)]
             L.orc_locate.restype = i32
             L.orc_locate.argtypes = [i32, i64, P, i64, P, P, P, P, P, i32]
+            L.orc_pair_dist.restype = i32
+            L.orc_pair_dist.argtypes = [i32, i64, P, i32, i64, P, i64, P, P, P, i32]
             L.orc_heuristic.restype = i32
             L.orc_heuristic.argtypes = [i32, i64, P, i32, i64, P, P, d, i32, i32, P, i64, P, P, P, P, i32]
             _lib = L
@@ -188,6 +190,21 @@ def cut(p, nodes, q, faces, pose=None, tol=1e-7, brute=False, ids=None, nthreads
     if rc != 0:
         raise ValueError("orc_cut rejected its arguments")
     return flags, dist, pflags, dict(zip(STAT_NAMES, (int(x) for x in stats)))
+
+
+def pair_dist(p, nodes, q, posed_faces, elem, face, nthreads=0):
+    """d(E, F) of element-face pairs: the minimum closed-triangle distance
+    between element elem[k]'s boundary triangles and face face[k]'s triangles
+    (faces already posed)."""
+    nodes, posed_faces = _f64(nodes), _f64(posed_faces)
+    elem = np.ascontiguousarray(elem, dtype=np.int64)
+    face = np.ascontiguousarray(face, dtype=np.int64)
+    out = np.zeros(elem.shape[0], dtype=np.float64)
+    rc = lib().orc_pair_dist(p, nodes.shape[0], _ptr(nodes), q, posed_faces.shape[0], _ptr(posed_faces),
+                             elem.shape[0], _ptr(elem), _ptr(face), _ptr(out), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_pair_dist rejected its arguments")
+    return out
 
 
 # ----------------------------------------------------------------- the paper's truncating variant

@@ -561,6 +561,46 @@ double orc_point_surface(const double *P, int64_t ntri, const double *tris, doub
     return best;
 }
 
+/* Distance of element-face pairs (Sec. 4.2, the curved element-face test of
+ * Alg. cp2, here over all triangles, with no truncation): d(E, F) = the
+ * minimum over E's 12 p^2 boundary triangles and F's 2 q^2 triangles of the
+ * closed-triangle distance.  For each of the n pairs (elem[k], face[k]) of the
+ * given (already posed) faces; OpenMP over the pairs.  The element-surface
+ * distance d(E) is the minimum of d(E, F) over all faces F.
+ * Returns 0, or -1 on bad arguments. */
+int orc_pair_dist(int p, int64_t n_elem, const double *nodes, int q, int64_t n_faces, const double *faces,
+                  int64_t n, const int64_t *elem, const int64_t *face, double *out, int nthreads) {
+    if (p < 1 || q < 1 || n_elem < 1 || n_faces < 1 || n < 0 || !nodes || !faces || !elem || !face || !out)
+        return -1;
+    for (int64_t k = 0; k < n; ++k)
+        if (elem[k] < 0 || elem[k] >= n_elem || face[k] < 0 || face[k] >= n_faces) return -1;
+    const int npe = (p + 1) * (p + 1) * (p + 1), npf = (q + 1) * (q + 1);
+    const int nte = 12 * p * p, ntf = 2 * q * q;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        double *etris = (double *)malloc(sizeof(double) * 9 * nte);
+        double *ftris = (double *)malloc(sizeof(double) * 9 * ntf);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < n; ++k) {
+            orc_elem_tris(p, nodes + 3 * npe * elem[k], etris);
+            orc_face_tris(q, faces + 3 * npf * face[k], ftris);
+            double best = INFINITY;
+            for (int i = 0; i < nte; ++i)
+                for (int j = 0; j < ntf; ++j) {
+                    double d = orc_tritri(etris + 9 * i, ftris + 9 * j, NULL, NULL);
+                    if (d < best) best = d;
+                }
+            out[k] = best;
+        }
+        free(etris);
+        free(ftris);
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* the paper's truncating variant (Sec. 4.2 and Alg. cp0, bboxdix, cp1, cp2)  */
 /* ------------------------------------------------------------------------ */

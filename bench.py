@@ -38,27 +38,42 @@ sys.path.insert(0, ROOT)
 METRIC = "cut ms & element-face tests/s at 64^3 Q2 hexes; p50/p99 cut latency, vs plain"
 UNIT = "element-face tests/s"
 WORKLOAD = "dimpled sphere (6144 Q2 faces, 336 dimples) cutting 64^3 Q2 hexes (262,144 elements, sinusoidal 0.1h)"
-# arithmetic of one full triangle-pair evaluation (paper_1711_07663_gb300/csrc/flopcount.cu:
-# mean over near pairs; FMA = 2 flops)
-FLOPS_PER_PAIR = 936.5
+# C_tt, the arithmetic of one triangle-triangle distance as the oracle's
+# routine computes it (tests/flops/oracle_flops.cpp: orc_tritri counted with a
+# counting number type, mean over near pairs): the per-unit cost of the
+# algorithmic count
+FLOPS_PER_PAIR = 2887.6
+# the same for the kernels' own FP32 routine (tests/flops/kernel_flops.cu; a
+# fused multiply-add counts 2): the per-pair cost of the executed-work figures
+FLOPS_PER_PAIR_KERNEL = 936.5
 # arithmetic of the plane-separation test every listed pair of the flags-only
 # stage takes (two normals 30, two norms 12, two thresholds 18, six signed
 # volumes 48, extrema and compares 16) plus its box test (15)
 FLOPS_PER_SEP = 139.0
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 # Alg. cp0 key of one (element, face) pair: 4 corners rotated into the OBB
 # axes (60), box distance (12), centroid distance (9), key (2)
 FLOPS_PER_KEY = 83.0
 # one Newton step of the donor search on a Q2 element: the 27-node map and
 # Jacobian (27 x 32), the 1-D bases (72) and the 3x3 solve (60)
 FLOPS_PER_NEWTON_STEP_Q2 = 996.0
+# DRAM bytes (read + write) of one k_near_main launch at the scale workload,
+# from the ncu capture summarised in profiles/k_near_main_scale64.md; None
+# until the current kernel has been captured
+K_NEAR_MAIN_TRAFFIC = None
 # resident-mesh bytes one cut must move: a FP32 box read and a flag written per
 # element, the FP32 frame of each element that needs the exact test (Q2: 27
 # nodes x 3 x 4 B), the FP64 face nodes (Q2: 9 x 3 x 8 B)
 BYTES_PER_ELEM = 25
 BYTES_PER_EXACT_ELEM = 324
 BYTES_PER_FACE = 216
+
+
+def bench_config(workload, n_elem, n_faces):
+    """The `config` object of both arms' JSON lines (the same keys and values
+    for the same workload)."""
+    return {"workload": WORKLOAD if workload == "scale64" else workload, "n_elem": int(n_elem),
+            "n_faces": int(n_faces), "p": 2, "q": 2,
+            "l2": "GPU arm: flushed (256 MB write) between timed steps; CPU oracle arm: not applicable"}
 
 
 def necessary(workload):
@@ -73,6 +88,43 @@ def measured_peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def alu_peaks(dev_index):
+    """FP32 and FP64 FMA peaks of this GPU, measured by bench_peaks.cu (8
+    independent FMA chains per thread, full occupancy, best of several
+    launches timed with CUDA events): the denominators of every ALU roofline
+    here.  Returns TFLOP/s and the SM count the device reports."""
+    import ctypes
+    import torch
+    from paper_1711_07663_gb300 import build as B
+    lib = ctypes.CDLL(B.build_peaks())
+    lib.bp_fma.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)]
+    lib.bp_fma.restype = ctypes.c_int
+    torch.cuda.set_device(dev_index)
+    out = {"sm_count": torch.cuda.get_device_properties(dev_index).multi_processor_count}
+    for name, fp64, iters, reps in (("fp32", 0, 1 << 16, 7), ("fp64", 1, 1 << 10, 5)):
+        ms, fl = ctypes.c_float(0.0), ctypes.c_double(0.0)
+        rc = lib.bp_fma(fp64, iters, 8, reps, ctypes.byref(ms), ctypes.byref(fl))
+        if rc != 0:
+            raise RuntimeError(f"FMA peak microbenchmark failed ({rc})")
+        out[f"{name}_tflops"] = fl.value / (ms.value * 1e-3) / 1e12
+        out[f"{name}_ms"] = ms.value
+    out["how"] = ("bench_peaks.cu: 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, "
+                  "best of several launches by CUDA events; 1 FMA = 2 flops")
+    return out
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
 
 
 def _scale64():
@@ -107,8 +159,14 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="launch shapes cubes_per_edge,bin_cubes,warps_per_cta,cands_per_warp instead of the "
                          "autotuner's (for runs under a profiler, whose timings would mislead the tuner)")
-    ap.add_argument("--serving-seconds", type=float, default=2.0,
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the open-loop serving measurement (0: skip it)")
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="timed runs of the 256-instance batch (0: skip it)")
+    ap.add_argument("--precision-steps", type=int, default=3,
+                    help="timed cuts of the 128^3 Q3 precision-stress workload per form (0: skip it)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the FMA peak measurement (rooflines then use the unit-count figure)")
     ap.add_argument("--locate-points", type=int, default=1 << 20,
                     help="points of the donor-search measurement (0: skip it)")
     ap.add_argument("--heuristic-steps", type=int, default=10,
@@ -229,10 +287,10 @@ def run_reference(args, world, rank):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "n_elem": case.n_elem,
-                                                         "n_faces": case.n_faces, "p": 2, "q": 2},
+        "dtype": "f64", "data": "synthetic", "config": bench_config(args.workload, case.n_elem, case.n_faces),
         "effective_rate": case.n_elem * case.n_faces / (ms * 1e-3),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -240,35 +298,34 @@ def run_reference(args, world, rank):
 # ----------------------------------------------------------------- serving
 def serving_measure(dc, W, dev, seconds, rate=200.0, seed=77):
     """Open-loop serving: requests arrive as a Poisson stream (mean `rate`
-    per second) for `seconds` after a 0.5 s warm-up, each a cut of one of the
+    per second) for `seconds` after a 1 s warm-up, each a cut of one of the
     resident 32^3 / 64^3 / 96^3 Q2 grids (probabilities 0.5 / 0.3 / 0.2) by the
     dimpled sphere turned 0.5 degrees per request.  A request is submitted at
-    its arrival (dc_submit; up to 4 in flight share the GPU) and its latency is
-    its completion (dc_poll) minus its arrival.  The plain path serves the same
-    stream one request at a time in arrival order with the FP64 exact stage:
-    each request's service time is measured with the GPU otherwise idle and
-    the FIFO queue is evaluated from those times.  Also: the saturated rate
-    (all requests offered at once)."""
+    its arrival (dc_submit, host face nodes copied by the call; up to 3 in
+    flight share the GPU, admitted as slots free up) and its latency is its
+    completion (dc_poll) minus its arrival.  The plain path serves the same
+    arrival stream one request at a time in arrival order (FIFO) with the
+    FP64 exact stage, each a synchronous dc_cut; its latency is measured the
+    same way.  Also: both paths' saturated rates (every request offered at
+    once)."""
     import torch
     sizes = (32, 64, 96)
     meshes = [torch.from_numpy(W.background(n, 2, sinusoid=0.1)).to(dev) for n in sizes]
-    faces = torch.from_numpy(W.dimpled_sphere_case(n=8, m=32, q=2).faces).to(dev)
+    faces_h = np.ascontiguousarray(W.dimpled_sphere_case(n=8, m=32, q=2).faces)
     g = np.random.default_rng(seed)
     axis = g.normal(size=3)
-    warm = 0.5
+    warm = 1.0
     t_arr = np.cumsum(g.exponential(1.0 / rate, size=int((seconds + warm) * rate * 2) + 16))
     t_arr = t_arr[t_arr < seconds + warm]
     n_req = t_arr.size
     which = g.choice(3, size=n_req, p=[0.5, 0.3, 0.2])
     poses = [np.concatenate([W.axis_rotation(axis, np.deg2rad(0.5 * k)), np.zeros((3, 1))], axis=1)
              for k in range(n_req)]
-    ring = 16
-    outs = [[torch.empty(n ** 3, dtype=torch.int8, device=dev) for _ in range(ring)] for n in sizes]
-    res = {}
-    with dc.Context([(2, m) for m in meshes], max_inflight=4) as ctx:
-        for k in range(3):   # graphs and arenas of each size
-            ctx.cut(k, 2, faces, outs[k][0])
-        torch.cuda.synchronize()
+    ring = 8
+    outs = [[np.empty(n ** 3, dtype=np.int8) for _ in range(ring)] for n in sizes]
+    keep = t_arr >= warm
+
+    def open_loop(submit, poll):
         lat = np.full(n_req, np.nan)
         done_t = np.full(n_req, np.nan)
         pending = {}
@@ -277,36 +334,51 @@ def serving_measure(dc, W, dev, seconds, rate=200.0, seed=77):
         while k < n_req or pending:
             now = time.perf_counter() - t0
             while k < n_req and t_arr[k] <= now:
-                try:
-                    tk = ctx.submit(int(which[k]), 2, faces, outs[which[k]][k % ring], pose=poses[k])
-                except dc.DirectCutError as e:
-                    if e.status != dc.DC_EBUSY:
-                        raise
+                tk = submit(k)
+                if tk is None:
                     break
                 pending[tk] = k
                 k += 1
             for tk in list(pending):
-                if ctx.poll(tk, timeout_us=0) == 0:
+                if poll(tk):
                     j = pending.pop(tk)
                     done_t[j] = time.perf_counter() - t0
                     lat[j] = done_t[j] - t_arr[j]
-        keep = t_arr >= warm
+        return lat, done_t
+
+    def summary(lat, done_t):
         L = lat[keep] * 1e3
-        span = done_t[keep].max() - t_arr[keep].min()
-        res.update({"arrival_rate_per_s": rate, "seconds": seconds, "requests": int(keep.sum()),
-                    "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
-                    "req_per_s": float(keep.sum() / span)})
+        return {"requests": int(keep.sum()), "p50_ms": float(np.percentile(L, 50)),
+                "p99_ms": float(np.percentile(L, 99)),
+                "req_per_s": float(keep.sum() / (done_t[keep].max() - t_arr[keep].min()))}
+
+    res = {"arrival_rate_per_s": rate, "seconds": seconds, "warmup_s": warm}
+    with dc.Context([(2, m) for m in meshes], max_inflight=4) as ctx:
+        # every serving slot warmed with every grid (arenas are reserved at
+        # creation; this captures each slot's launch graphs)
+        for w in range(3):
+            tks = [ctx.submit(w, 2, faces_h, outs[w][j], pose=poses[0]) for j in range(3)]
+            for tk in tks:
+                ctx.poll(tk, timeout_us=-1)
+
+        def submit(k):
+            try:
+                return ctx.submit(int(which[k]), 2, faces_h, outs[which[k]][k % ring], pose=poses[k])
+            except dc.DirectCutError as e:
+                if e.status != dc.DC_EBUSY:
+                    raise
+                return None
+
+        lat, done_t = open_loop(submit, lambda tk: ctx.poll(tk, timeout_us=0) == 0)
+        res.update(summary(lat, done_t))
         # saturated: every request offered at once
         pending = {}
         k = 0
         t1 = time.perf_counter()
         while k < n_req or pending:
             while k < n_req:
-                try:
-                    tk = ctx.submit(int(which[k]), 2, faces, outs[which[k]][k % ring], pose=poses[k])
-                except dc.DirectCutError as e:
-                    if e.status != dc.DC_EBUSY:
-                        raise
+                tk = submit(k)
+                if tk is None:
                     break
                 pending[tk] = k
                 k += 1
@@ -314,26 +386,172 @@ def serving_measure(dc, W, dev, seconds, rate=200.0, seed=77):
                 if ctx.poll(tk, timeout_us=0) == 0:
                     pending.pop(tk)
         res["saturated_req_per_s"] = float(n_req / (time.perf_counter() - t1))
-    # the plain path: FP64 exact stage, one request at a time
-    with dc.Context([(2, m) for m in meshes], precision=dc.DC_FP64) as pctx:
-        for k in range(3):
-            pctx.cut(k, 2, faces, outs[k][0])
-        torch.cuda.synchronize()
-        svc = np.zeros(n_req)
+    # the plain path: FP64 exact stage, one request on the GPU at a time,
+    # served in arrival order
+    with dc.Context([(2, m) for m in meshes], precision=dc.DC_FP64, max_inflight=1) as pctx:
+        for w in range(3):
+            pctx.cut(w, 2, faces_h, outs[w][0], pose=poses[0])
+        lat = np.full(n_req, np.nan)
+        done_t = np.full(n_req, np.nan)
+        t0 = time.perf_counter()
         for k in range(n_req):
-            a = time.perf_counter()
-            pctx.cut(int(which[k]), 2, faces, outs[which[k]][k % ring], pose=poses[k])
-            svc[k] = time.perf_counter() - a
-    end = np.zeros(n_req)
-    prev = 0.0
-    for k in range(n_req):
-        end[k] = max(t_arr[k], prev) + svc[k]
-        prev = end[k]
-    keep = t_arr >= warm
-    PL = (end - t_arr)[keep] * 1e3
-    res["plain_fp64_fifo"] = {"p50_ms": float(np.percentile(PL, 50)), "p99_ms": float(np.percentile(PL, 99)),
-                              "req_per_s": float(keep.sum() / (end[keep].max() - t_arr[keep].min())),
-                              "saturated_req_per_s": float(1.0 / svc.mean())}
+            while time.perf_counter() - t0 < t_arr[k]:
+                pass
+            pctx.cut(int(which[k]), 2, faces_h, outs[which[k]][k % ring], pose=poses[k])
+            done_t[k] = time.perf_counter() - t0
+            lat[k] = done_t[k] - t_arr[k]
+        plain = summary(lat, done_t)
+        t1 = time.perf_counter()
+        for k in range(n_req):
+            pctx.cut(int(which[k]), 2, faces_h, outs[which[k]][k % ring], pose=poses[k])
+        plain["saturated_req_per_s"] = float(n_req / (time.perf_counter() - t1))
+    res["plain_fp64_fifo"] = plain
+    res["how"] = ("host face nodes and host flags through dc_submit / dc_poll (3 serving slots) against a "
+                  "DC_FP64 context serving the same arrivals one synchronous dc_cut at a time")
+    return res
+
+
+# ----------------------------------------------------------------- batching
+def batch_measure(dc, W, dev, stream, flush, steps=5):
+    """The 256-instance batch (8^3 to 40^3 Q2 grids, cubed spheres of 6 m^2
+    Q2 faces, random rotation and offset each) as one dc_cut_batch with the
+    autotuned launch shapes, against the plain path: the same 256 requests as
+    single synchronous FP64 cuts one after another.  Requests per second of
+    each (host wall time of the whole batch, inputs resident on the device,
+    L2 flushed before each), device time of the batch by CUDA events, and
+    whether the flags agree."""
+    import torch
+    t0 = time.perf_counter()
+    cases = W.batch_cases()
+    gen_s = time.perf_counter() - t0
+    meshes = [(cs.p, torch.from_numpy(cs.nodes).to(dev)) for cs in cases]
+    fdev = {}
+    for cs in cases:
+        key = id(cs.faces)
+        if key not in fdev:
+            fdev[key] = torch.from_numpy(cs.faces).to(dev)
+    outs = [torch.empty(cs.n_elem, dtype=torch.int8, device=dev) for cs in cases]
+    reqs = [dict(q=cs.q, faces=fdev[id(cs.faces)], flags_out=o, pose=cs.pose, stream=stream.cuda_stream)
+            for cs, o in zip(cases, outs)]
+    idx = list(range(len(cases)))
+    res = {"instances": len(cases), "elements": int(sum(cs.n_elem for cs in cases)),
+           "faces": int(sum(cs.n_faces for cs in cases)), "generate_s": gen_s}
+    with dc.Context(meshes, precision=dc.DC_FP32_RECHECK) as ctx:
+        tuning, trials = ctx.autotune(idx, reqs, repeats=3)
+        for _ in range(2):
+            ctx.cut_batch(idx, reqs)
+        wall, dev_ms = [], []
+        for k in range(steps):
+            flush.fill_(k & 0xff)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t1 = time.perf_counter()
+            ctx.cut_batch(idx, reqs)
+            wall.append(time.perf_counter() - t1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dev_ms.append(a.elapsed_time(b))
+        st = ctx.stats()
+    fl32 = [o.clone() for o in outs]
+    with dc.Context(meshes, precision=dc.DC_FP64, max_inflight=1, reserve_faces=-1) as pctx:
+        for i in idx[:8]:
+            pctx.cut(i, reqs[i]["q"], reqs[i]["faces"], outs[i], pose=reqs[i]["pose"], stream=stream.cuda_stream)
+        flush.fill_(0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for i in idx:
+            pctx.cut(i, reqs[i]["q"], reqs[i]["faces"], outs[i], pose=reqs[i]["pose"], stream=stream.cuda_stream)
+        plain_s = time.perf_counter() - t1
+    same = all(bool(torch.equal(a, b)) for a, b in zip(fl32, outs))
+    bw = float(np.median(wall))
+    res.update({"tuning": dict(tuning, trials=trials), "batch_ms": bw * 1e3,
+                "batch_device_ms": float(np.median(dev_ms)), "req_per_s": len(cases) / bw,
+                "candidates": st["n_candidates"],
+                "plain_fp64_sequential": {"ms": plain_s * 1e3, "req_per_s": len(cases) / plain_s},
+                "speedup_req_per_s": (len(cases) / bw) / (len(cases) / plain_s), "same_flags": same,
+                "how": "dc_cut_batch of all 256 (FP32 bulk + FP64 re-solve, autotuned) vs 256 synchronous "
+                       "DC_FP64 dc_cut calls; wall time, inputs resident, L2 flushed before each timing"})
+    return res
+
+
+# ----------------------------------------------------------------- precision stress
+def precision_measure(dc, W, dev, stream, flush, steps=3):
+    """The precision-stress workload: 128^3 Q3 hexes (2,097,152 elements,
+    3.2 GB FP64) against a Q3 sphere of 6*32*32 faces, with the lattice
+    vertices the oracle-side script placed within 1e-4 h of the linearised
+    surface (tests/golden/precision_stress.npz; the grazing fraction of the
+    necessary pair set is the oracle's count).  The FP32 bulk with FP64
+    re-solve against all-FP64: cut times, flag agreement (distance and flags-
+    only forms), re-solve counts, and the distribution of the FP32 stage's own
+    distance error |d32 - d64| / h over the exact-test elements."""
+    import torch
+    G = np.load(os.path.join(ROOT, "tests", "golden", "precision_stress.npz"))
+    n, p, m, q = int(G["n"]), int(G["p"]), int(G["m"]), int(G["q"])
+    h = 4.0 / n
+    t0 = time.perf_counter()
+    lat = W.hex_lattice(n, p)
+    lat.reshape(-1, 3)[G["idx"]] = G["coords"]
+    lat_d = torch.from_numpy(lat).to(dev).reshape(-1, 3)
+    del lat
+    gi = torch.from_numpy(W.gather_index(n, p)).to(dev)
+    nodes = lat_d[gi.reshape(-1)].reshape(n ** 3, (p + 1) ** 3, 3).contiguous()
+    del gi, lat_d
+    faces = torch.from_numpy(W.cubed_sphere(m, q, radius=1.0)).to(dev)
+    gen_s = time.perf_counter() - t0
+    NE = n ** 3
+    res = {"elements": NE, "faces": int(faces.shape[0]), "p": p, "q": q, "pi_g": float(G["pi_g"]),
+           "moved_vertices": int(G["idx"].size), "s_star_pairs": int(G["s_star_pairs"]),
+           "grazing_pairs": int(G["grazing_pairs"]), "crossing_pairs": int(G["crossing_pairs"]),
+           "grazing_fraction": int(G["grazing_pairs"]) / int(G["s_star_pairs"]),
+           "grazing_definition": "S* pairs with 0 < d(E,F) < 1e-4 h (oracle count)", "generate_s": gen_s}
+    out = {}
+    for name, prec in (("fp32_recheck", dc.DC_FP32_RECHECK), ("fp64", dc.DC_FP64)):
+        f = torch.empty(NE, dtype=torch.int8, device=dev)
+        d = torch.empty(NE, dtype=torch.float64, device=dev)
+        d32 = torch.empty(NE, dtype=torch.float32, device=dev) if prec == dc.DC_FP32_RECHECK else None
+        g = torch.empty(NE, dtype=torch.int8, device=dev)
+        with dc.Context([(p, nodes)], precision=prec) as ctx:
+            ctx.cut(0, q, faces, f, d, stream=stream.cuda_stream, fp32_dist_out=d32)
+            st = ctx.stats()
+            ctx.cut(0, q, faces, g, stream=stream.cuda_stream)
+            ms, ms_f = [], []
+            for k in range(steps):
+                for form, lst in ((d, ms), (None, ms_f)):
+                    flush.fill_(k & 0xff)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    ctx.cut(0, q, faces, f if form is not None else g, form, stream=stream.cuda_stream)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    lst.append(a.elapsed_time(b))
+        out[name] = (f.cpu().numpy(), d.cpu().numpy(), None if d32 is None else d32.cpu().numpy(), g.cpu().numpy(),
+                     st, float(np.median(ms)), float(np.median(ms_f)))
+    del nodes
+    f32, dd32, e32, g32, s32, ms32, msf32 = out["fp32_recheck"]
+    f64, dd64, _, g64, s64, ms64, msf64 = out["fp64"]
+    fin = np.isfinite(dd64) & np.isfinite(e32) & ~np.isnan(e32)
+    err = np.abs(e32[fin].astype(np.float64) - dd64[fin]) / h
+    edges = [0.0] + [10.0 ** k for k in range(-14, -3)] + [np.inf]
+    hist, _ = np.histogram(err, bins=edges)
+    zero = int((err == 0).sum())
+    res.update({
+        "fp32_recheck": {"dist_ms": ms32, "flags_only_ms": msf32, "pairs_fp32": s32["pairs_bulk"],
+                         "pairs_fp64_resolved": s32["pairs_recheck"], "fp64_redo_elements": s32["fallbacks"],
+                         "candidates": s32["n_candidates"]},
+        "fp64": {"dist_ms": ms64, "flags_only_ms": msf64, "pairs_fp64": s64["pairs_bulk"]},
+        "speedup_dist": ms64 / ms32, "speedup_flags_only": msf64 / msf32,
+        "same_flags": bool(np.array_equal(f32, f64) and np.array_equal(g32, g64) and np.array_equal(f32, g32)),
+        "fp32_error_over_h": {"elements": int(fin.sum()), "exactly_zero": zero,
+                              "bins_upper_edges": [float(x) for x in edges[1:]],
+                              "counts": [int(c) - (zero if i == 0 else 0) for i, c in enumerate(hist)],
+                              "max": float(err.max()) if err.size else None,
+                              "median": float(np.median(err)) if err.size else None,
+                              "note": "counts per bin (edges[i], edges[i+1]]; elements with error exactly 0 "
+                                      "listed apart"},
+    })
     return res
 
 
@@ -351,8 +569,18 @@ def run_ours(args, world, rank, local):
 
     if rank == 0 or not os.path.exists(dc.lib_path()):
         B.build()
+        B.build_peaks()
     barrier(world)
     dc.load()
+    # the ALU rooflines' denominators, measured on this GPU before anything else
+    peaks = None if args.no_peaks else alu_peaks(local)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+
+    def fp32_peak(sm_max):
+        if peaks:
+            return peaks["fp32_tflops"], "measured (bench_peaks.cu)"
+        return n_sm * 128 * 2 * sm_max * 1e6 / 1e12, f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
+
     case = WORKLOADS[args.workload]()
     NE, NF = case.n_elem, case.n_faces
     nodes = torch.from_numpy(case.nodes).to(dev)
@@ -507,7 +735,7 @@ def run_ours(args, world, rank, local):
         # the paper's variant per candidate: every face's key, 16 faces x 12
         # corner-triangle pairs, 4 faces x 3 element faces x 2p^2 x 2q^2 pairs
         hflops = ncand_h * (NF * FLOPS_PER_KEY + (16 * 12 + 4 * 3 * 2 * case.p ** 2 * 2 * case.q ** 2) * FLOPS_PER_PAIR)
-        hpeak = SM_COUNT * FP32_LANES_PER_SM * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        hpeak = fp32_peak(clocks.get("sm_max_mhz") or 2070.0)[0]
         heur = {"ms": float(np.median(hms)), "disagree": int((ex != hv).sum()),
                 "roofline": {"bound": "alu", "achieved": hflops / (float(np.median(hms)) * 1e-3) / 1e12, "peak": hpeak,
                              "unit": "TFLOP/s", "frac": hflops / (float(np.median(hms)) * 1e-3) / 1e12 / hpeak,
@@ -562,7 +790,7 @@ def run_ours(args, world, rank, local):
         # algorithmic: Newton to convergence on every candidate box (4 steps
         # each) -- the containment checks the paper's search leaves
         pflops = pst["candidates"] * 4 * FLOPS_PER_NEWTON_STEP_Q2
-        ppeak = SM_COUNT * FP32_LANES_PER_SM * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        ppeak = fp32_peak(clocks.get("sm_max_mhz") or 2070.0)[0]
         pconn = {"elements": int(shell.shape[0]), "points": args.locate_points, "ms": lm,
                  "roofline": {"bound": "alu", "achieved": pflops / (lm * 1e-3) / 1e12, "peak": ppeak, "unit": "TFLOP/s",
                               "frac": pflops / (lm * 1e-3) / 1e12 / ppeak, "flops": pflops,
@@ -573,6 +801,9 @@ def run_ours(args, world, rank, local):
                  "candidates": pst["candidates"], "fp64_steps": pst["fp64_steps"], "tree_depth": pst["tree_depth"]}
 
     serving = serving_measure(dc, W, dev, args.serving_seconds) if args.serving_seconds > 0 else None
+    batch = batch_measure(dc, W, dev, stream, flush, args.batch_steps) if args.batch_steps > 0 else None
+    precision = (precision_measure(dc, W, dev, stream, flush, args.precision_steps)
+                 if args.precision_steps > 0 else None)
 
     # cold: the grid is not resident -- create the context from pinned host
     # nodes (upload, element boxes and frames), cut once, destroy it
@@ -588,25 +819,33 @@ def run_ours(args, world, rank, local):
 
     # roofline of the dominant kernel (the flags-only exact stage): ALU bound.
     # Algorithmic arithmetic = the exact test on the necessary pair set S*:
-    # |S*| x n_Tc x n_T(F) triangle pairs x the flops of one triangle pair, with
-    # n_Tc = the 3 element faces at the nearest corner (lower count) or all 6
-    # (upper).  Executed arithmetic (what this kernel runs): every listed
-    # triangle pair takes the separation test, the undecided ones the full test.
+    # |S*| x n_Tc x n_T(F) triangle pairs x C_tt (the oracle's triangle-pair
+    # routine), with n_Tc = the 3 element faces at the nearest corner (lower
+    # count) or all 6 (upper).  Executed arithmetic (what this kernel runs):
+    # every listed triangle pair takes the separation test, the undecided ones
+    # the kernels' full test.
     ex_ms = float(np.mean(exact_ms))
     pairs = float(np.mean(bulk))
     pairs_full = float(np.mean(full))
-    flops_exec = pairs * FLOPS_PER_SEP + pairs_full * FLOPS_PER_PAIR
+    flops_exec = pairs * FLOPS_PER_SEP + pairs_full * FLOPS_PER_PAIR_KERNEL
     flops_alg = S_STAR * nec["n_tc_lower"] * nec["n_tf"] * FLOPS_PER_PAIR
     flops_alg_upper = S_STAR * nec["n_tc_upper"] * nec["n_tf"] * FLOPS_PER_PAIR
     achieved = flops_alg / (ex_ms * 1e-3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak, peak_basis = fp32_peak(sm_max)
+    fp64_peak = peaks["fp64_tflops"] if peaks else None
     # the whole cut: T* = max(bytes / HBM peak, flops / FP32 peak)
     hbm = measured_peaks().get("hbm_gbs")
     cut_bytes = NE * BYTES_PER_ELEM + nec["exact_test_elements"] * BYTES_PER_EXACT_ELEM + NF * BYTES_PER_FACE
     t_bytes_us = cut_bytes / (hbm * 1e9) * 1e6 if hbm else None
     t_flops_us = flops_alg / (peak * 1e12) * 1e6
     t_star_us = max(t_flops_us, t_bytes_us or 0.0)
+    # the plain FP64 path against the FP64 peak (the same algorithmic count)
+    plain_roofline = None
+    if plain_ms and fp64_peak:
+        plain_roofline = {"bound": "alu", "achieved": flops_alg / (plain_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                          "unit": "TFLOP/s", "frac": flops_alg / (plain_ms * 1e-3) / 1e12 / fp64_peak,
+                          "scope": "whole plain DC_FP64 cut, S* algorithmic flops", "peak_basis": "measured FP64 FMA"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -615,7 +854,7 @@ def run_ours(args, world, rank, local):
         cpu = {"value": S_STAR * done / NE / dt, "unit": UNIT, "cores": ncpu, "kind": "oracle",
                "sample": f"{done} random elements of the workload ({dt:.1f} s, all {ncpu} host threads); "
                          f"one cut = the sampled time scaled to all {NE} elements",
-               "single_thread_value": S_STAR * d1 / NE / t1}
+               "single_thread_value": S_STAR * d1 / NE / t1, "cpu_model": cpu_model()}
 
     if rank == 0:
         line = {
@@ -623,10 +862,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "effective_rate": world * NE * NF / (ms_per_step * 1e-3), "s_star_pairs": S_STAR,
-            "config": {"workload": WORKLOAD if args.workload == "scale64" else args.workload, "n_elem": NE, "n_faces": NF, "p": 2, "q": 2,
-                       "precision": "fp32 bulk + fp64 re-solve", "mesh": "resident",
-                       "l2": "flushed (256 MB write) between timed steps",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(args.workload, NE, NF),
+            "precision": "fp32 bulk + fp64 re-solve", "mesh": "resident", "parallelism": f"replicas x{world}",
             "cut_ms_p50": float(np.percentile(step_ms, 50)), "cut_ms_p99": float(np.percentile(step_ms, 99)),
             "plain_fp64_ms": plain_ms, "speedup_vs_plain": (plain_ms / float(np.median(step_ms))) if plain_ms else None,
             "plain_same_flags": same_flags,
@@ -646,21 +883,31 @@ def run_ours(args, world, rank, local):
             "gpu_launches": 9 * args.steps,
             "roofline": {"bound": "alu", "kernel": "k_near_main (flags-only exact stage)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch,
-                         # from an ncu capture of the current kernel; none has been
-                         # taken since the full search moved out of it
-                         "traffic": None,
+                         # dram__bytes_read.sum + dram__bytes_write.sum of one launch of
+                         # the current kernel (ncu, profiles/k_near_main_scale64.md)
+                         "traffic": K_NEAR_MAIN_TRAFFIC,
                          "flops_per_launch": flops_alg, "flops_upper_count": flops_alg_upper,
                          "units": f"|S*| = {S_STAR} element-face pairs x {nec['n_tc_lower']} x {nec['n_tf']} "
-                                  f"triangle pairs x {FLOPS_PER_PAIR} flops",
-                         "executed_flops": flops_exec, "executed_tflops": flops_exec / (ex_ms * 1e-3) / 1e12,
-                         "pairs_per_launch": pairs, "pairs_full_test": pairs_full,
-                         "flops_per_pair": {"separation": FLOPS_PER_SEP, "full": FLOPS_PER_PAIR},
-                         "duration_ms": ex_ms,
-                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+                                  f"triangle pairs x C_tt = {FLOPS_PER_PAIR} flops (the oracle's triangle routine)",
+                         "note": "frac above 1: the kernel settles the flags with less arithmetic than the "
+                                 "method's exact test on S* (certified plane separation and crossings); its "
+                                 "own limit is latency, see executed",
+                         "executed": {"flops": flops_exec, "tflops": flops_exec / (ex_ms * 1e-3) / 1e12,
+                                      "frac_fp32_peak": flops_exec / (ex_ms * 1e-3) / 1e12 / peak,
+                                      "dram_bytes": K_NEAR_MAIN_TRAFFIC,
+                                      "frac_hbm": (K_NEAR_MAIN_TRAFFIC / (ex_ms * 1e-3) / (hbm * 1e9)
+                                                   if (K_NEAR_MAIN_TRAFFIC and hbm) else None),
+                                      "pairs": pairs, "pairs_full_test": pairs_full,
+                                      "flops_per_pair": {"separation": FLOPS_PER_SEP, "full": FLOPS_PER_PAIR_KERNEL}},
+                         "duration_ms": ex_ms, "peak_basis": peak_basis},
             "cut_roofline": {"t_star_us": t_star_us, "t_flops_us": t_flops_us, "t_bytes_us": t_bytes_us,
                              "bytes": cut_bytes, "hbm_gbs": hbm, "frac": t_star_us / (ms_per_step * 1e3),
-                             "bound": "alu" if t_flops_us >= (t_bytes_us or 0.0) else "hbm"},
+                             "bound": "alu" if t_flops_us >= (t_bytes_us or 0.0) else "hbm",
+                             "peak_tflops": peak},
+            "plain_fp64_roofline": plain_roofline,
+            "alu_peaks": peaks,
+            "batch256": batch,
+            "precision_stress": precision,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

@@ -35,9 +35,12 @@
  *                  (hole) or +HUGE_VAL (field).
  *
  * Ownership: the caller owns every pointer it passes.  dc_create copies the
- * meshes to the device; dc_cut and dc_submit read the request's inputs before
- * returning.  Output buffers must stay valid until dc_cut returns, or until
- * dc_poll reports completion of a submitted ticket.
+ * meshes to the device.  dc_cut reads the request's inputs before it returns.
+ * dc_submit copies host face nodes and the pose into library-owned memory
+ * before it returns, so the caller may overwrite them at once; device face
+ * nodes are read by the cut on the GPU and must stay unchanged until dc_poll
+ * reports completion.  Output buffers must stay valid until dc_cut returns, or
+ * until dc_poll reports completion of a submitted ticket.
  *
  * Errors: no exception crosses this ABI.  Every call returns a dc_status; the
  * text of the calling thread's last error is available from dc_last_error().
@@ -106,6 +109,13 @@ typedef struct {
     int32_t bin_cubes;        /* hole-map cubes per face bin along each axis, 1..16; 0 -> 4 */
     int32_t max_inflight;     /* serving slots for dc_submit, 1..64; 0 -> 4 */
     int32_t profile;          /* 1: time each phase with CUDA events (dc_get_stats) */
+    int32_t reserve_faces;    /* dc_create sizes every slot's device arena and pinned
+                                 staging for one request of this many order-4 faces on
+                                 the largest mesh, so requests up to that size never
+                                 allocate (larger ones grow the slot first); 0 -> 8192,
+                                 -1 -> reserve nothing (grow on first use).  A
+                                 reservation that would exceed mem_budget_bytes is
+                                 skipped. */
 } dc_config;
 
 typedef struct {
@@ -120,6 +130,14 @@ typedef struct {
                                  enqueueing on `stream`; results are valid once the
                                  stream reaches that point */
     void *stream;             /* cudaStream_t for dc_cut; NULL = the context's stream */
+    float *fp32_dist_out;     /* optional [n_elem], DC_FP32_RECHECK with dist_out only, dc_cut /
+                                 dc_cut_batch only: each exact-test element's distance as the
+                                 FP32 bulk alone computed it (the smallest FP32 triangle-pair
+                                 distance, signed as dist_out) before any FP64 re-solve, for
+                                 reporting the FP32 error; NaN where the FP32 stage computed
+                                 none (elements settled by their node labels, or redone in
+                                 FP64), +-inf where the hole map decided.  Same memory kind
+                                 as dist_out.  NULL: not written. */
 } dc_request;
 
 typedef struct {
@@ -169,8 +187,10 @@ dc_status dc_cut(dc_ctx *ctx, int32_t mesh, const dc_request *req);
 dc_status dc_cut_batch(dc_ctx *ctx, int32_t n, const int32_t *meshes, const dc_request *reqs);
 
 /* Serving: admit a request into a free slot (DC_EBUSY when none is free or the
- * memory budget is exhausted), copy its inputs, enqueue the cut on the slot's
- * stream and return a ticket.  Requests in different slots overlap on the GPU. */
+ * memory budget is exhausted), copy its host inputs (face nodes into the
+ * slot's pinned staging, the pose), enqueue the cut on the slot's stream and
+ * return a ticket.  Requests in different slots overlap on the GPU.  A request
+ * within the slot's reservation (dc_config.reserve_faces) allocates nothing. */
 dc_status dc_submit(dc_ctx *ctx, int32_t mesh, const dc_request *req, uint64_t *ticket);
 
 /* Wait up to timeout_us (0 = just test, <0 = wait until done) for a ticket:
@@ -225,13 +245,18 @@ dc_status dc_autotune(dc_ctx *ctx, int32_t n, const int32_t *meshes, const dc_re
 /* Drain in-flight work, then free everything the context owns. */
 void dc_destroy(dc_ctx *ctx);
 
-/* Message for the calling thread's last failing call ("" if none). */
-const char *dc_last_error(void);
+/* Message of the calling thread's last failing call ("" if none).  Messages
+ * are kept per thread, not per context: ctx may be NULL (as for the calls that
+ * take no context), and a context used from several threads gives each thread
+ * its own message. */
+const char *dc_last_error(const dc_ctx *ctx);
 
 /* Allocation-free cut, for callers that cannot allocate device memory at the
- * time they cut: code running under CUDA stream capture (cudaMalloc cannot be
- * captured), loops that forbid allocation after start-up, and hosts whose own
- * allocator must own all device memory.  The paper has no counterpart; it is
+ * time they cut: real-time loops that forbid allocation after start-up
+ * (cudaMalloc and cudaFree may block and synchronise the device, so their
+ * latency has no bound) and hosts whose own allocator owns all device memory
+ * (a caching pool that reserves the GPU's memory up front, where a second
+ * allocator would fail or fragment it).  The paper has no counterpart; it is
  * the cut of dc_cut for one background grid, without a context.
  *
  *   nodes       device pointer, [n_elem][(p+1)^3][3] float64 (not copied)
@@ -239,7 +264,7 @@ const char *dc_last_error(void);
  *   pose        host pointer to 12 doubles [R|t], or NULL
  *   tol         fringe tolerance; 0 -> 1e-7
  *   flags_out   device pointer, [n_elem] int8 (required)
- *   dist_out    device pointer, [n_elem] float64, or NULL
+ *   dist_out    device pointer, [n_elem] float64, or NULL (flags only)
  *   stream      cudaStream_t to run on (NULL: the legacy default stream);
  *               the call returns after that stream has finished the cut.
  *
@@ -255,13 +280,13 @@ const char *dc_last_error(void);
  *
  * All calls in a process share the array, which keeps the last call's
  * contents; each call resets what must start at zero.  Calls are serialised
- * by a lock in the library; work on that array that overlapped on the GPU
- * (another thread's stream running a call while a new one starts) would race,
- * which the lock and the final stream synchronisation prevent.
+ * by a lock in the library, and each returns only after its stream has
+ * finished (on an error too, once work was queued), so two calls never use the
+ * array at once; work on the array that overlapped on the GPU would race.
  *
  * The first call on a device sets up (looks up the array's device address,
  * uploads the triangle tables, sets kernel attributes) with that device
- * current; make that first call before any stream capture begins. */
+ * current. */
 dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double *nodes, int32_t q, int64_t n_faces,
                          const double *face_nodes, const double *pose, double tol, int8_t *flags_out,
                          double *dist_out, void *stream);

@@ -59,13 +59,14 @@ class dc_mesh_desc(ctypes.Structure):
 class dc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t),
                 ("tol", ctypes.c_double), ("holemap_cells", ctypes.c_int32), ("bin_cubes", ctypes.c_int32),
-                ("max_inflight", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("max_inflight", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserve_faces", ctypes.c_int32)]
 
 
 class dc_request(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("n_faces", ctypes.c_int64), ("face_nodes", ctypes.c_void_p),
                 ("pose", ctypes.c_void_p), ("flags_out", ctypes.c_void_p), ("dist_out", ctypes.c_void_p),
-                ("on_device", ctypes.c_int32), ("async_", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("on_device", ctypes.c_int32), ("async_", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("fp32_dist_out", ctypes.c_void_p)]
 
 
 class dc_stats(ctypes.Structure):
@@ -122,7 +123,7 @@ def load(build_if_missing: bool = False):
         L.dc_get_stats.restype = i32
         L.dc_destroy.argtypes = [P]
         L.dc_destroy.restype = None
-        L.dc_last_error.argtypes = []
+        L.dc_last_error.argtypes = [P]
         L.dc_last_error.restype = ctypes.c_char_p
         L.dc_version.argtypes = []
         L.dc_version.restype = ctypes.c_char_p
@@ -153,8 +154,10 @@ def load(build_if_missing: bool = False):
         return L
 
 
-def dc_last_error() -> str:
-    return load().dc_last_error().decode()
+def dc_last_error(ctx=None) -> str:
+    """The calling thread's last error message (messages are per thread; ctx
+    may be given or not)."""
+    return load().dc_last_error(ctx).decode()
 
 
 def dc_version() -> str:
@@ -173,7 +176,8 @@ def _addr(x, dtype):
         return None, False, None
     if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
         import torch
-        want = {np.float64: torch.float64, np.int8: torch.int8, np.uint8: torch.uint8, np.int64: torch.int64}[dtype]
+        want = {np.float64: torch.float64, np.float32: torch.float32, np.int8: torch.int8, np.uint8: torch.uint8,
+                np.int64: torch.int64}[dtype]
         if x.dtype != want or not x.is_contiguous():
             raise TypeError(f"tensor must be contiguous {want}")
         return x.data_ptr(), bool(x.is_cuda), x
@@ -208,13 +212,16 @@ def dc_create(meshes, **cfg_kw):
     return h.value
 
 
-def _request(q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=False):
+def _request(q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=False, fp32_dist_out=None):
     r = dc_request()
     fp, fdev, fk = _addr(faces, np.float64)
     op, odev, ok = _addr(flags_out, np.int8)
     dp, ddev, dk = _addr(dist_out, np.float64)
+    sp, sdev, sk = _addr(fp32_dist_out, np.float32)
     if dist_out is not None and ddev != odev:
         raise ValueError("flags_out and dist_out must live in the same memory")
+    if fp32_dist_out is not None and sdev != odev:
+        raise ValueError("flags_out and fp32_dist_out must live in the same memory")
     if fdev != odev:
         raise ValueError("face nodes and outputs must both be host or both be device memory")
     pk = None
@@ -229,21 +236,24 @@ def _request(q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=
     r.on_device = int(fdev)
     r.async_ = int(bool(async_))
     r.stream = None if stream is None else int(stream)
-    return r, (fk, ok, dk, pk)
+    r.fp32_dist_out = sp
+    return r, (fk, ok, dk, pk, sk)
 
 
-def dc_cut(ctx, mesh, q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=False):
-    r, keep = _request(q, faces, flags_out, dist_out, pose, stream, async_)
+def dc_cut(ctx, mesh, q, faces, flags_out, dist_out=None, pose=None, stream=None, async_=False, fp32_dist_out=None):
+    r, keep = _request(q, faces, flags_out, dist_out, pose, stream, async_, fp32_dist_out)
     _check(load().dc_cut(ctx, int(mesh), ctypes.byref(r)))
 
 
 def dc_cut_batch(ctx, meshes, requests):
-    """requests: list of dicts with keys q, faces, flags_out[, dist_out, pose]."""
+    """requests: list of dicts with keys q, faces, flags_out[, dist_out, pose,
+    fp32_dist_out, stream] (the batch runs on the first request's stream)."""
     n = len(requests)
     arr = (dc_request * n)()
     keep = []
     for i, rq in enumerate(requests):
-        r, k = _request(rq["q"], rq["faces"], rq["flags_out"], rq.get("dist_out"), rq.get("pose"))
+        r, k = _request(rq["q"], rq["faces"], rq["flags_out"], rq.get("dist_out"), rq.get("pose"),
+                        stream=rq.get("stream"), fp32_dist_out=rq.get("fp32_dist_out"))
         arr[i] = r
         keep.append(k)
     ms = (ctypes.c_int32 * n)(*[int(m) for m in meshes])
@@ -269,15 +279,30 @@ def dc_get_stats(ctx) -> dict:
 
 
 def dc_cut_noalloc(p, nodes, q, faces, flags_out, dist_out=None, pose=None, tol=0.0, stream=None):
-    """Allocation-free cut (device tensors only): see dc_cut_noalloc in the header."""
+    """Allocation-free cut (device tensors only): see dc_cut_noalloc in the
+    header.  For callers that may not allocate device memory when they cut
+    (allocation-free real-time loops, hosts whose own allocator owns the
+    GPU's memory).  Shapes are checked here, so that a short output or a
+    flattened node array is a ValueError instead of an out-of-bounds access
+    on the device."""
     np_, ndev, nk = _addr(nodes, np.float64)
     fp, fdev, fk = _addr(faces, np.float64)
     op, odev, ok = _addr(flags_out, np.int8)
     dp, ddev, dk = _addr(dist_out, np.float64)
     if not (ndev and fdev and odev and (dist_out is None or ddev)):
         raise ValueError("dc_cut_noalloc takes device tensors only")
+    p, q = int(p), int(q)
+    if tuple(nk.shape[1:]) != ((p + 1) ** 3, 3) or nk.dim() != 3:
+        raise ValueError(f"nodes must have shape [n_elem][{(p + 1) ** 3}][3] for p={p}, got {tuple(nk.shape)}")
+    if tuple(fk.shape[1:]) != ((q + 1) ** 2, 3) or fk.dim() != 3:
+        raise ValueError(f"faces must have shape [n_faces][{(q + 1) ** 2}][3] for q={q}, got {tuple(fk.shape)}")
+    n_elem = int(nk.shape[0])
+    if ok.numel() < n_elem:
+        raise ValueError(f"flags_out holds {ok.numel()} entries, {n_elem} needed")
+    if dk is not None and dk.numel() < n_elem:
+        raise ValueError(f"dist_out holds {dk.numel()} entries, {n_elem} needed")
     pk = None if pose is None else np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
-    _check(load().dc_cut_noalloc(int(p), int(nk.shape[0]), np_, int(q), int(fk.shape[0]), fp,
+    _check(load().dc_cut_noalloc(p, n_elem, np_, q, int(fk.shape[0]), fp,
                                  None if pk is None else pk.ctypes.data, float(tol), op, dp,
                                  None if stream is None else int(stream)))
 
@@ -372,7 +397,8 @@ def dc_autotune(ctx, meshes, requests, repeats=3):
     arr = (dc_request * n)()
     keep = []
     for i, rq in enumerate(requests):
-        r, k = _request(rq["q"], rq["faces"], rq["flags_out"], rq.get("dist_out"), rq.get("pose"))
+        r, k = _request(rq["q"], rq["faces"], rq["flags_out"], rq.get("dist_out"), rq.get("pose"),
+                        stream=rq.get("stream"))
         arr[i] = r
         keep.append(k)
     ms = (ctypes.c_int32 * n)(*[int(m) for m in meshes])
@@ -445,11 +471,12 @@ class Context:
         self.n_elem = [int(n.shape[0]) for _, n in self.meshes]
         self.handle = dc_create(self.meshes, **cfg)
 
-    def cut(self, mesh, q, faces, flags_out=None, dist_out=None, pose=None, stream=None, async_=False):
+    def cut(self, mesh, q, faces, flags_out=None, dist_out=None, pose=None, stream=None, async_=False,
+            fp32_dist_out=None):
         if flags_out is None:
             n = self.n_elem[mesh] if 0 <= mesh < len(self.n_elem) else 1
             flags_out = np.empty(n, dtype=np.int8)
-        dc_cut(self.handle, mesh, q, faces, flags_out, dist_out, pose, stream, async_)
+        dc_cut(self.handle, mesh, q, faces, flags_out, dist_out, pose, stream, async_, fp32_dist_out)
         return flags_out
 
     def cut_batch(self, meshes, requests):

@@ -50,5 +50,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+PEAKS_SRC = os.path.join(ROOT, "bench_peaks.cu")
+PEAKS_LIB = os.path.join(ROOT, "_build", "libbenchpeaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """The benchmark's FP32/FP64 FMA peak microbenchmark (bench_peaks.cu at the
+    repository root) into _build/libbenchpeaks.so; not part of the library."""
+    os.makedirs(os.path.dirname(PEAKS_LIB), exist_ok=True)
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + f".{os.getpid()}.tmp"
+    subprocess.run([_nvcc(), *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, PEAKS_SRC],
+                   check=True)
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

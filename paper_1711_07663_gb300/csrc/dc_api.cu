@@ -24,6 +24,7 @@
 #include "dc_overset.cuh"
 #include "dc_heur.cuh"
 #include "dc_pc.cuh"
+#include "dc_frames.cuh"
 
 using namespace dc;
 
@@ -49,49 +50,23 @@ dc_status fail(dc_status st, const char* fmt, ...) {
 
 // ------------------------------------------------------------------ element boxes
 // Node boxes rounded outward and, when loc/org are given, the element frame of
-// the exact test: origin at the centre of the float box, node coordinates
-// relative to it rounded to float (the values every exact-test kernel uses).
-__global__ void k_elem_box(const double* __restrict__ nodes, long long n_elem, int npe, float* __restrict__ box,
-                           float* __restrict__ loc, double* __restrict__ org, int* __restrict__ bad,
-                           double* __restrict__ ext_sum) {
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ext_sum) {
-    // sum of the elements' longest box sides (warp sums, then one atomic each)
-    double ext = 0.0;
-    if (e < n_elem) {
-      const double* y = nodes + e * npe * 3;
-      double lo[3] = {y[0], y[1], y[2]}, hi[3] = {y[0], y[1], y[2]};
-      for (int k = 1; k < npe; ++k)
-        for (int a = 0; a < 3; ++a) { lo[a] = fmin(lo[a], y[3 * k + a]); hi[a] = fmax(hi[a], y[3 * k + a]); }
-      ext = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
-      if (!(ext < 1e300)) ext = 0.0;
-    }
-    for (int s = 16; s; s >>= 1) ext += __shfl_xor_sync(0xffffffffu, ext, s);
-    if ((threadIdx.x & 31) == 0 && ext > 0.0) atomicAdd(ext_sum, ext);
-  }
-  if (e >= n_elem) return;
-  const double* x = nodes + e * npe * 3;
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  bool nonfinite = false;
-  for (int k = 0; k < npe; ++k)
-    for (int a = 0; a < 3; ++a) {
-      double v = x[3 * k + a];
-      nonfinite |= !(fabs(v) < 1e300);
-      lo[a] = fmin(lo[a], v);
-      hi[a] = fmax(hi[a], v);
-    }
-  double o[3];
-  for (int a = 0; a < 3; ++a) {
-    const float bl = __double2float_rd(lo[a]), bh = __double2float_ru(hi[a]);
-    box[6 * e + a] = bl;
-    box[6 * e + 3 + a] = bh;
-    o[a] = 0.5 * ((double)bl + (double)bh);
-  }
-  if (nonfinite) atomicOr(bad, 1);
-  if (!loc) return;
-  for (int a = 0; a < 3; ++a) org[3 * e + a] = o[a];
-  for (int k = 0; k < npe; ++k)
-    for (int a = 0; a < 3; ++a) loc[e * 3 * npe + a * npe + k] = (float)(x[3 * k + a] - o[a]);
+// the exact test (k_elem_frames, dc_frames.cuh): a persistent grid of blocks
+// over tiles of consecutive elements.  bad[0] is set for a non-finite node,
+// bad[1] when a bulk copy never completed; ext_sum (may be null) receives the
+// sum of the elements' longest box sides.
+cudaError_t launch_frames(const double* nodes, long long n_elem, int npe, float* box, float* loc, double* org,
+                          int* bad, double* ext_sum, int n_sm, cudaStream_t st) {
+  const int eb = frames_tile_elems(npe);
+  const size_t sm = frames_smem(npe);
+  cudaError_t e = cudaFuncSetAttribute(k_elem_frames, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_elem_frames, FR_THREADS, sm);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (n_elem + eb - 1) / eb;
+  const long long grid = std::min<long long>(tiles, (long long)n_sm * std::max(occ, 1));
+  k_elem_frames<<<(unsigned)grid, FR_THREADS, sm, st>>>(nodes, n_elem, npe, eb, box, loc, org, bad, ext_sum, bad + 1);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ triangle tables
@@ -143,8 +118,6 @@ struct Mesh {
   long long n_elem = 0;
   double* nodes = nullptr;
   float* box = nullptr;
-  float* loc = nullptr;    // element-frame node coordinates [n_elem][3][npe]
-  double* org = nullptr;   // element frame origins [n_elem][3]
   float h_elem = 0.f;      // mean longest box side of the elements
 };
 
@@ -167,6 +140,7 @@ struct LaunchParams {
   // flags-only form of the exact stage (k_near_*), when some instance
   // asks for flags only
   bool near = false;
+  bool uniform = false;  // every instance has element order pmax and face order qmax
   int wpc = 8, cpw = 1;  // its warps per block and candidates per cursor step
   int* hsel = nullptr;   // truncating variant: kept faces per candidate
   unsigned long long* full = nullptr;  // flags-only stage: candidates for the full search
@@ -174,7 +148,8 @@ struct LaunchParams {
     return n == o.n && nf_total == o.nf_total && ne_total == o.ne_total && max_tri == o.max_tri && max_f == o.max_f &&
            pmax == o.pmax &&
            qmax == o.qmax && precision == o.precision && prof == o.prof && d_inst == o.d_inst && d_off == o.d_off &&
-           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && wpc == o.wpc && cpw == o.cpw &&
+           cand == o.cand && redo == o.redo && d_cnt == o.d_cnt && near == o.near && uniform == o.uniform &&
+           wpc == o.wpc && cpw == o.cpw &&
            hsel == o.hsel && full == o.full;
   }
 };
@@ -208,6 +183,12 @@ struct Slot {
   int8_t* h_flags = nullptr;     // pinned output staging (serving, host outputs)
   double* h_dist = nullptr;
   size_t h_out_cap = 0;
+  // pinned copy of a submitted request's host face nodes: dc_submit copies
+  // them here before it returns, and the upload reads this copy, so the caller
+  // may reuse its buffer at once (a slot is reused only after its ticket is
+  // collected, so the copy is never overwritten while its upload is pending)
+  double* h_faces = nullptr;
+  size_t h_faces_cap = 0;         // doubles
   bool busy = false;
   uint64_t ticket = 0;
   // in-flight bookkeeping
@@ -247,6 +228,13 @@ struct dc_ctx {
   int near_dyn_max = 0;  // dynamic shared memory k_near_main may take per block
   dc_tuning tune{1.8f, 4, 8, 1, 0.f};  // launch shapes (dc_set_tuning, dc_autotune)
   bool use_graphs = true;  // replay captured launch sequences (DC_NO_GRAPHS=1 disables)
+  // the slots' reservation made at creation: one pinned host block and one
+  // device block, carved into every slot's staging and arena (buffers a slot
+  // later outgrows are replaced by its own allocations)
+  char* pin_block = nullptr;
+  size_t pin_bytes = 0;
+  char* dev_block = nullptr;
+  size_t dev_bytes = 0;
 };
 
 namespace {
@@ -310,14 +298,40 @@ cudaError_t launch_rows(bool pdl, Inst* d_inst, const long long* foff, int n, lo
   return launch_k(pdl, k_row_label, dim3((MAX_DIM * MAX_DIM + 7) / 8, n), dim3(256), 0, st, d_inst);
 }
 
-// bytes of arena a batch needs
-size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
+// the flags-only stage's kernel for a batch: compiled for its orders when
+// every instance has the same element order p and face order q (p = q, the
+// workloads' case), otherwise the form that reads the orders per instance
+using NearKernel = void (*)(Inst*, CandList, CandList, NearBufs, int, int, int, unsigned long long*);
+NearKernel near_kernel(int pmax, int qmax, bool uniform) {
+  if (uniform && pmax == qmax) {
+    switch (pmax) {
+      case 1: return k_near_main<1, 1>;
+      case 2: return k_near_main<2, 2>;
+      case 3: return k_near_main<3, 3>;
+      case 4: return k_near_main<4, 4>;
+      default: break;
+    }
+  }
+  return k_near_main<0, 0>;
+}
+const NearKernel NEAR_KERNELS[] = {k_near_main<0, 0>, k_near_main<1, 1>, k_near_main<2, 2>, k_near_main<3, 3>,
+                                   k_near_main<4, 4>};
+
+// one instance's surface as far as the arena is concerned
+struct SurfNeed {
+  long long F;  // faces
+  int q;        // their order
+  bool staged;  // host faces, uploaded into the arena
+};
+
+// bytes of arena a batch of surfaces over ne_total elements needs
+size_t arena_bytes(const dc_ctx* c, const std::vector<SurfNeed>& v, long long ne_total) {
   size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
   int nb = nbins_cap(bin_floor(c->cfg));
   for (auto& r : v) {
-    long long F = r.req->n_faces;
-    int npf = (r.req->q + 1) * (r.req->q + 1);
-    if (!r.req->on_device) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
+    long long F = r.F;
+    int npf = (r.q + 1) * (r.q + 1);
+    if (r.staged) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
     if (c->cfg.precision == DC_HEURISTIC) s += al256(sizeof(float) * 16 * F);
     s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(float) * F * 6) +
          al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) +
@@ -326,8 +340,29 @@ size_t arena_need(dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) 
   s += al256(sizeof(unsigned long long) * ne_total) * 3;  // candidates, redo, full-search list
   if (c->cfg.precision == DC_HEURISTIC) s += al256(sizeof(int) * HEUR_SEL * ne_total);  // kept faces
   s += al256(sizeof(unsigned long long) * NCNT);
-  s += al256(ne_total) + al256(sizeof(double) * ne_total);  // output staging (host outputs)
+  s += al256(ne_total) + al256(sizeof(double) * ne_total) + al256(sizeof(float) * ne_total);  // output staging
   return s;
+}
+
+size_t arena_need(const dc_ctx* c, const std::vector<InstReq>& v, long long ne_total) {
+  std::vector<SurfNeed> sv;
+  sv.reserve(v.size());
+  for (auto& r : v) sv.push_back({r.req->n_faces, r.req->q, !r.req->on_device});
+  return arena_bytes(c, sv, ne_total);
+}
+
+// free a slot's buffer unless it is part of the context's reservation
+void host_free(const dc_ctx* c, void* p) {
+  if (!p) return;
+  const char* q = static_cast<const char*>(p);
+  if (c->pin_block && q >= c->pin_block && q < c->pin_block + c->pin_bytes) return;
+  cudaFreeHost(p);
+}
+void dev_free(const dc_ctx* c, void* p) {
+  if (!p) return;
+  const char* q = static_cast<const char*>(p);
+  if (c->dev_block && q >= c->dev_block && q < c->dev_block + c->dev_bytes) return;
+  cudaFree(p);
 }
 
 dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
@@ -343,7 +378,7 @@ dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
     CK(cudaStreamSynchronize(s.stream));
     for (auto& g : s.graphs) cudaGraphExecDestroy(g.exec);
     s.graphs.clear();
-    CK(cudaFree(s.arena.base));
+    dev_free(c, s.arena.base);
     c->arena_bytes -= s.arena.cap;
     s.arena.base = nullptr;
     s.arena.cap = 0;
@@ -358,12 +393,12 @@ dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
   return DC_OK;
 }
 
-dc_status ensure_host(Slot& s, size_t n_inst, long long ne_total) {
+dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total) {
   if (s.h_inst_cap < n_inst) {
     for (int r = 0; r < Slot::RING; ++r) {
       if (s.ring_used[r]) CK(cudaEventSynchronize(s.ring_ev[r]));
-      if (s.ring_inst[r]) cudaFreeHost(s.ring_inst[r]);
-      if (s.ring_off[r]) cudaFreeHost(s.ring_off[r]);
+      host_free(c, s.ring_inst[r]);
+      host_free(c, s.ring_off[r]);
       s.ring_inst[r] = nullptr;
       s.ring_off[r] = nullptr;
       s.ring_used[r] = false;
@@ -385,14 +420,28 @@ dc_status ensure_host(Slot& s, size_t n_inst, long long ne_total) {
   }
   if (!s.h_cnt) CK(cudaMallocHost(&s.h_cnt, sizeof(unsigned long long) * NCNT));
   if ((long long)s.h_out_cap < ne_total) {
-    if (s.h_flags) cudaFreeHost(s.h_flags);
-    if (s.h_dist) cudaFreeHost(s.h_dist);
+    host_free(c, s.h_flags);
+    host_free(c, s.h_dist);
     s.h_flags = nullptr;
     s.h_dist = nullptr;
     CK(cudaMallocHost(&s.h_flags, (size_t)ne_total));
     CK(cudaMallocHost(&s.h_dist, sizeof(double) * ne_total));
     s.h_out_cap = (size_t)ne_total;
   }
+  return DC_OK;
+}
+
+// pinned staging for a submitted request's host face nodes (n doubles)
+dc_status ensure_face_stage(dc_ctx* c, Slot& s, size_t n) {
+  if (s.h_faces_cap >= n) return DC_OK;
+  host_free(c, s.h_faces);
+  s.h_faces = nullptr;
+  s.h_faces_cap = 0;
+  if (cudaMallocHost(&s.h_faces, sizeof(double) * n) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DC_ENOMEM, "cudaMallocHost(%zu) for the face staging failed", sizeof(double) * n);
+  }
+  s.h_faces_cap = n;
   return DC_OK;
 }
 
@@ -405,6 +454,8 @@ dc_status validate_req(dc_ctx* c, int mesh, const dc_request* r) {
   if (r->pose)
     for (int i = 0; i < 12; ++i)
       if (!std::isfinite(r->pose[i])) return fail(DC_EINVAL, "pose has a non-finite entry");
+  if (r->fp32_dist_out && (!r->dist_out || c->cfg.precision != DC_FP32_RECHECK))
+    return fail(DC_EINVAL, "fp32_dist_out needs dist_out and the DC_FP32_RECHECK precision");
   // face nodes are checked on the device as they are posed (k_surface), for
   // host and device inputs alike
   return DC_OK;
@@ -474,12 +525,13 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     if (per * wpc > (size_t)c->near_dyn_max)
       return fail(DC_EINVAL, "orders p=%d q=%d need %zu bytes of shared memory per warp", pmax, qmax, per);
     const size_t sm = per * wpc;
+    const NearKernel kn = near_kernel(pmax, qmax, P.uniform);
     int occn = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, k_near_main, 32 * wpc, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, kn, 32 * wpc, sm);
     occn = std::max(occn, 1);
     CandList fl{P.full, (unsigned long long)ne_total, d_cnt + 20};
-    CK(launch_k(true, k_near_main, dim3(c->n_sm * occn), dim3(32 * wpc), sm, st, d_inst, cl, fl, nb, pmax, qmax,
-                P.cpw, d_cnt + 4));
+    CK(launch_k(true, kn, dim3(c->n_sm * occn), dim3(32 * wpc), sm, st, d_inst, cl, fl, nb, pmax, qmax, P.cpw,
+                d_cnt + 4));
     // the candidates it listed for the full per-element search -- only
     // elements with no labelled node that are not fringe (distances are never
     // asked for in this form), almost always none: a small FP64 pass
@@ -541,11 +593,17 @@ dc_status launch_graph(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t s
 }
 
 // Enqueue the whole cut of a batch on slot s (no host synchronisation).
-dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool staged_out) {
+// copy_inputs: the call returns before the cut has read its inputs (dc_submit),
+// so host face nodes are first copied into the slot's pinned staging; the
+// synchronous calls upload straight from the caller's buffer, which stays
+// valid until they return.
+dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool copy_inputs) {
   const int n = (int)v.size();
   long long nf_total = 0, ne_total = 0, max_tri = 0, max_f = 0;
-  int pmax = 1, qmax = 1;
+  int pmax = 1, qmax = 1, pmin = MAX_P, qmin = MAX_Q;
   for (auto& r : v) {
+    pmin = std::min(pmin, c->meshes[r.mesh].p);
+    qmin = std::min(qmin, r.req->q);
     nf_total += r.req->n_faces;
     max_f = std::max<long long>(max_f, r.req->n_faces);
     ne_total += c->meshes[r.mesh].n_elem;
@@ -555,8 +613,16 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   }
   dc_status rc = ensure_arena(c, s, arena_need(c, v, ne_total));
   if (rc) return rc;
-  rc = ensure_host(s, (size_t)n, ne_total);
+  rc = ensure_host(c, s, (size_t)n, ne_total);
   if (rc) return rc;
+  size_t host_face_doubles = 0;
+  if (copy_inputs) {
+    for (auto& r : v)
+      if (!r.req->on_device) host_face_doubles += (size_t)r.req->n_faces * (r.req->q + 1) * (r.req->q + 1) * 3;
+    rc = ensure_face_stage(c, s, host_face_doubles);
+    if (rc) return rc;
+  }
+  size_t hf_off = 0;
   // carve the arena
   char* p = s.arena.base;
   auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return r; };
@@ -573,8 +639,6 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     int npf = (r->q + 1) * (r->q + 1);
     in.nodes = m.nodes;
     in.eaabb = m.box;
-    in.eloc = m.loc;
-    in.eorg = m.org;
     in.n_elem = m.n_elem;
     in.p = m.p;
     in.q = r->q;
@@ -583,7 +647,14 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
       in.faces_in = r->face_nodes;
     } else {
       double* stage = (double*)take(sizeof(double) * F * npf * 3);
-      CK(cudaMemcpyAsync(stage, r->face_nodes, sizeof(double) * F * npf * 3, cudaMemcpyHostToDevice, st));
+      const size_t nd = (size_t)F * npf * 3;
+      const double* src = r->face_nodes;
+      if (copy_inputs) {
+        memcpy(s.h_faces + hf_off, r->face_nodes, sizeof(double) * nd);
+        src = s.h_faces + hf_off;
+        hf_off += nd;
+      }
+      CK(cudaMemcpyAsync(stage, src, sizeof(double) * nd, cudaMemcpyHostToDevice, st));
       in.faces_in = stage;
     }
     in.has_pose = r->pose ? 1 : 0;
@@ -624,6 +695,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   unsigned long long* d_cnt = (unsigned long long*)take(sizeof(unsigned long long) * NCNT);
   int8_t* oflags = (int8_t*)take(ne_total);
   double* odist = (double*)take(sizeof(double) * ne_total);
+  float* od32 = (float*)take(sizeof(float) * ne_total);
   // outputs: caller's device buffers, or staging for host buffers
   long long off = 0;
   for (int i = 0; i < n; ++i) {
@@ -632,13 +704,14 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     if (r->on_device) {
       in.flags = r->flags_out;
       in.dist = r->dist_out;
+      in.dist32 = r->fp32_dist_out;
     } else {
       in.flags = oflags + off;
       in.dist = r->dist_out ? odist + off : nullptr;
+      in.dist32 = r->fp32_dist_out ? od32 + off : nullptr;
     }
     off += in.n_elem;
   }
-  (void)staged_out;
 
   CK(cudaMemcpyAsync(d_inst, s.h_inst, sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_off, s.h_off, sizeof(long long) * 2 * (n + 1), cudaMemcpyHostToDevice, st));
@@ -650,6 +723,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   lp.d_inst = d_inst; lp.d_off = d_off; lp.cand = cand; lp.redo = redo; lp.d_cnt = d_cnt; lp.hsel = hsel;
   lp.full = fulll;
   lp.wpc = c->tune.warps_per_cta; lp.cpw = c->tune.cands_per_warp;
+  lp.uniform = pmin == pmax && qmin == qmax;
   {
     // the flags-only form when no instance asks for distances (a batch that
     // mixes both runs the distance form for all)
@@ -726,6 +800,8 @@ dc_status copy_out_host(Slot& s, const std::vector<InstReq>& v, cudaStream_t st)
     if (!r->on_device) {
       CK(cudaMemcpyAsync(r->flags_out, s.h_inst[i].flags, (size_t)ne, cudaMemcpyDeviceToHost, st));
       if (r->dist_out) CK(cudaMemcpyAsync(r->dist_out, s.h_inst[i].dist, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
+      if (r->fp32_dist_out)
+        CK(cudaMemcpyAsync(r->fp32_dist_out, s.h_inst[i].dist32, sizeof(float) * ne, cudaMemcpyDeviceToHost, st));
     }
   }
   return DC_OK;
@@ -744,15 +820,16 @@ void free_slot(dc_ctx* c, Slot& s) {
   if (s.stream) cudaStreamSynchronize(s.stream);
   for (auto& g : s.graphs) cudaGraphExecDestroy(g.exec);
   s.graphs.clear();
-  if (s.arena.base) { cudaFree(s.arena.base); c->arena_bytes -= s.arena.cap; }
+  if (s.arena.base) { dev_free(c, s.arena.base); c->arena_bytes -= s.arena.cap; }
   for (int r = 0; r < Slot::RING; ++r) {
-    if (s.ring_inst[r]) cudaFreeHost(s.ring_inst[r]);
-    if (s.ring_off[r]) cudaFreeHost(s.ring_off[r]);
+    host_free(c, s.ring_inst[r]);
+    host_free(c, s.ring_off[r]);
     if (s.ring_ev[r]) cudaEventDestroy(s.ring_ev[r]);
   }
-  if (s.h_cnt) cudaFreeHost(s.h_cnt);
-  if (s.h_flags) cudaFreeHost(s.h_flags);
-  if (s.h_dist) cudaFreeHost(s.h_dist);
+  host_free(c, s.h_cnt);
+  host_free(c, s.h_flags);
+  host_free(c, s.h_dist);
+  host_free(c, s.h_faces);
   for (int i = 0; i < 6; ++i)
     if (s.ev[i]) cudaEventDestroy(s.ev[i]);
   if (s.done) cudaEventDestroy(s.done);
@@ -765,7 +842,10 @@ void free_slot(dc_ctx* c, Slot& s) {
 // ------------------------------------------------------------------ public ABI
 extern "C" {
 
-const char* dc_last_error(void) { return g_err.c_str(); }
+const char* dc_last_error(const dc_ctx* ctx) {
+  (void)ctx;  // the message belongs to the calling thread, whatever the context
+  return g_err.c_str();
+}
 
 const char* dc_version(void) { return "directcut 0.1 (sm_103a)"; }
 
@@ -778,6 +858,7 @@ dc_status dc_config_default(dc_config* cfg) {
   cfg->holemap_cells = 0;
   cfg->bin_cubes = 4;
   cfg->max_inflight = 4;
+  cfg->reserve_faces = 8192;
   return DC_OK;
 }
 
@@ -790,6 +871,9 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
   if (cfg.tol == 0.0) cfg.tol = 1e-7;
   if (cfg.bin_cubes == 0) cfg.bin_cubes = 4;
   if (cfg.max_inflight == 0) cfg.max_inflight = 4;
+  if (cfg.reserve_faces == 0) cfg.reserve_faces = 8192;
+  if (cfg.reserve_faces < -1 || cfg.reserve_faces > (1 << 24))
+    return fail(DC_EINVAL, "reserve_faces outside -1..%d", 1 << 24);
   if (!(cfg.tol > 0.0) || !std::isfinite(cfg.tol)) return fail(DC_EINVAL, "tol must be positive and finite");
   if (cfg.holemap_cells != 0 && (cfg.holemap_cells < 8 || cfg.holemap_cells > MAX_CELLS))
     return fail(DC_EINVAL, "holemap_cells outside 8..%d (or 0: automatic)", MAX_CELLS);
@@ -827,16 +911,21 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     cudaFuncAttributes fe, fd;
     if (cudaFuncGetAttributes(&fe, k_exact<float>) != cudaSuccess || cudaFuncGetAttributes(&fd, k_exact<double>) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
-    cudaFuncAttributes fnm;
-    if (cudaFuncGetAttributes(&fnm, k_near_main) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
+    size_t near_static = 0;
+    for (NearKernel kn : NEAR_KERNELS) {
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, kn) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaFuncGetAttributes failed"));
+      near_static = std::max(near_static, fa.sharedSizeBytes);
+    }
     if (cudaFuncSetAttribute(k_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fe.sharedSizeBytes)) != cudaSuccess ||
-        cudaFuncSetAttribute(k_near_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(c->smem_optin - fnm.sharedSizeBytes)) != cudaSuccess ||
         cudaFuncSetAttribute(k_exact<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->smem_optin - fd.sharedSizeBytes)) != cudaSuccess)
       return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
-    c->near_dyn_max = (int)(c->smem_optin - fnm.sharedSizeBytes);
+    c->near_dyn_max = (int)(c->smem_optin - near_static);
+    for (NearKernel kn : NEAR_KERNELS)
+      if (cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->near_dyn_max) != cudaSuccess)
+        return bail(fail(DC_ECUDA, "cudaFuncSetAttribute failed"));
     cudaFuncAttributes fhf, fhd;
     if (cudaFuncGetAttributes(&fhf, k_heur_final<float>) != cudaSuccess ||
         cudaFuncGetAttributes(&fhd, k_heur_final<double>) != cudaSuccess ||
@@ -852,7 +941,7 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     dc_status st = init_slot(s, cfg.profile);
     if (st) return bail(st);
   }
-  int* d_bad = nullptr;  // [0]: a node is not finite; bytes 8..15: sum of element extents
+  int* d_bad = nullptr;  // [0]: a node is not finite; [1]: a node copy failed; bytes 8..15: sum of extents
   if (cudaMalloc(&d_bad, 16) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
   double* d_ext = reinterpret_cast<double*>(reinterpret_cast<char*>(d_bad) + 8);
   cudaStream_t st = c->slots[0].stream;
@@ -865,41 +954,97 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     c->pmax = std::max(c->pmax, md.p);
     size_t npe = (size_t)(md.p + 1) * (md.p + 1) * (md.p + 1);
     size_t nb = sizeof(double) * npe * 3 * md.n_elem, bb = sizeof(float) * 6 * md.n_elem;
-    size_t lb = sizeof(float) * npe * 3 * md.n_elem, ob = sizeof(double) * 3 * md.n_elem;
-    if (cfg.mem_budget_bytes && c->mesh_bytes + nb + bb + lb + ob > cfg.mem_budget_bytes) {
+    if (cfg.mem_budget_bytes && c->mesh_bytes + nb + bb > cfg.mem_budget_bytes) {
       cudaFree(d_bad);
       return bail(fail(DC_ENOMEM, "mesh %d does not fit the memory budget", i));
     }
-    if (cudaMalloc(&m.nodes, nb) != cudaSuccess || cudaMalloc(&m.box, bb) != cudaSuccess ||
-        cudaMalloc(&m.loc, lb) != cudaSuccess || cudaMalloc(&m.org, ob) != cudaSuccess) {
+    if (cudaMalloc(&m.nodes, nb) != cudaSuccess || cudaMalloc(&m.box, bb) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(d_bad);
-      return bail(fail(DC_ENOMEM, "mesh %d: cudaMalloc of %zu bytes failed", i, nb + bb + lb + ob));
+      return bail(fail(DC_ENOMEM, "mesh %d: cudaMalloc of %zu bytes failed", i, nb + bb));
     }
-    c->mesh_bytes += nb + bb + lb + ob;
+    c->mesh_bytes += nb + bb;
     cudaMemcpyKind kind = md.nodes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (cudaMemcpyAsync(m.nodes, md.nodes, nb, kind, st) != cudaSuccess) {
       cudaFree(d_bad);
       return bail(fail(DC_ECUDA, "mesh %d: copying nodes failed", i));
     }
     cudaMemsetAsync(d_bad, 0, 16, st);
-    k_elem_box<<<(unsigned)((md.n_elem + 255) / 256), 256, 0, st>>>(m.nodes, md.n_elem, (int)npe, m.box, m.loc, m.org,
-                                                                      d_bad, d_ext);
-    int bad = 0;
+    const cudaError_t fe = launch_frames(m.nodes, md.n_elem, (int)npe, m.box, nullptr, nullptr, d_bad, d_ext, c->n_sm, st);
+    int bad[2] = {0, 0};
     double ext = 0.0;
-    if (cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (fe != cudaSuccess || cudaMemcpyAsync(bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(&ext, d_ext, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaStreamSynchronize(st);
       cudaFree(d_bad);
-      return bail(fail(DC_ECUDA, "mesh %d: element boxes failed: %s", i, cudaGetErrorString(cudaGetLastError())));
+      return bail(fail(DC_ECUDA, "mesh %d: element boxes failed: %s", i,
+                       cudaGetErrorString(fe != cudaSuccess ? fe : cudaGetLastError())));
     }
-    if (bad) {
+    if (bad[1]) {
+      cudaFree(d_bad);
+      return bail(fail(DC_EINTERNAL, "mesh %d: a bulk copy of element nodes did not complete", i));
+    }
+    if (bad[0]) {
       cudaFree(d_bad);
       return bail(fail(DC_EINVAL, "mesh %d has a NaN or infinite node", i));
     }
     m.h_elem = (float)(ext / (double)md.n_elem);
   }
   cudaFree(d_bad);
+  if (cfg.reserve_faces > 0) {
+    // every slot sized now for one request on the largest mesh, so that
+    // dc_cut and dc_submit of such requests allocate nothing while serving
+    long long ne_max = 0;
+    for (auto& m : c->meshes) ne_max = std::max(ne_max, m.n_elem);
+    const std::vector<SurfNeed> one{{(long long)cfg.reserve_faces, MAX_Q, true}};
+    const size_t need = al256(arena_bytes(c, one, ne_max));
+    const size_t stage = (size_t)cfg.reserve_faces * (MAX_Q + 1) * (MAX_Q + 1) * 3;
+    const size_t n_slots = c->slots.size();
+    auto serving = [&](size_t i) { return i > 0 || n_slots == 1; };
+    // host staging of one slot: instance ring, counters, outputs, and the
+    // face copy of a submitted request (serving slots)
+    const size_t ring_one = al256(sizeof(Inst)) + al256(sizeof(long long) * 4);
+    auto host_need = [&](size_t i) {
+      return Slot::RING * ring_one + al256(sizeof(unsigned long long) * NCNT) + al256((size_t)ne_max) +
+             al256(sizeof(double) * ne_max) + (serving(i) ? al256(sizeof(double) * stage) : 0);
+    };
+    size_t host_total = 0;
+    for (size_t i = 0; i < n_slots; ++i) host_total += host_need(i);
+    if (!cfg.mem_budget_bytes || c->mesh_bytes + need * n_slots <= cfg.mem_budget_bytes) {
+      if (cudaMalloc(&c->dev_block, need * n_slots) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(DC_ENOMEM, "cudaMalloc(%zu) for the slots' arenas failed", need * n_slots));
+      }
+      c->dev_bytes = need * n_slots;
+      if (cudaMallocHost(&c->pin_block, host_total) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(DC_ENOMEM, "cudaMallocHost(%zu) for the slots' staging failed", host_total));
+      }
+      c->pin_bytes = host_total;
+      char* hp = c->pin_block;
+      auto take = [&](size_t bytes) { char* r = hp; hp += al256(bytes); return r; };
+      for (size_t i = 0; i < n_slots; ++i) {
+        Slot& s = c->slots[i];
+        s.arena.base = c->dev_block + i * need;
+        s.arena.cap = need;
+        c->arena_bytes += need;
+        for (int r = 0; r < Slot::RING; ++r) {
+          s.ring_inst[r] = reinterpret_cast<Inst*>(take(sizeof(Inst)));
+          s.ring_off[r] = reinterpret_cast<long long*>(take(sizeof(long long) * 4));
+        }
+        s.h_inst_cap = 1;
+        s.h_cnt = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * NCNT));
+        s.h_flags = reinterpret_cast<int8_t*>(take((size_t)ne_max));
+        s.h_dist = reinterpret_cast<double*>(take(sizeof(double) * ne_max));
+        s.h_out_cap = (size_t)ne_max;
+        if (serving(i)) {
+          s.h_faces = reinterpret_cast<double*>(take(sizeof(double) * stage));
+          s.h_faces_cap = stage;
+        }
+      }
+    }
+  }
   *out = c;
   return DC_OK;
 }
@@ -1068,6 +1213,7 @@ dc_status dc_submit(dc_ctx* c, int32_t mesh, const dc_request* req, uint64_t* ti
   std::lock_guard<std::mutex> lk(c->mu);
   dc_status rc = validate_req(c, mesh, req);
   if (rc) return rc;
+  if (req->fp32_dist_out) return fail(DC_EINVAL, "fp32_dist_out is for dc_cut and dc_cut_batch");
   CK(cudaSetDevice(c->cfg.device));
   // slot 0 stays reserved for dc_cut; serving uses the others (or slot 0 when
   // only one exists)
@@ -1139,11 +1285,11 @@ void dc_destroy(dc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->cfg.device);
   for (auto& s : c->slots) free_slot(c, s);
+  if (c->pin_block) cudaFreeHost(c->pin_block);
+  if (c->dev_block) cudaFree(c->dev_block);
   for (auto& m : c->meshes) {
     if (m.nodes) cudaFree(m.nodes);
     if (m.box) cudaFree(m.box);
-    if (m.loc) cudaFree(m.loc);
-    if (m.org) cudaFree(m.org);
   }
   delete c;
 }
@@ -1151,16 +1297,17 @@ void dc_destroy(dc_ctx* c) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ allocation-free cut
-// Some callers cannot allocate device memory when they cut: code that runs
-// while a stream is being captured into a CUDA graph (cudaMalloc is not a
-// capturable call), real-time loops that forbid allocation after start-up, and
-// hosts whose own allocator must own every device byte.  dc_cut_noalloc serves
-// them: the same cut as dc_cut, with every scratch buffer carved from the
-// fixed array below, which each GPU that loads this library holds until the
-// process exits.  In host code `g_noalloc_scratch` only names a host-side
-// stand-in for the symbol, never a device address: the address the kernels
-// get comes from cudaGetSymbolAddress, once per device, with that device
-// current.
+// Some callers cannot allocate device memory when they cut: real-time loops
+// that forbid allocation after start-up (cudaMalloc and cudaFree may block and
+// synchronise the device, so their latency has no bound), and hosts whose own
+// allocator owns every device byte (a framework's caching pool that reserves
+// the GPU's memory up front, where a second allocator would fail or fragment
+// it).  dc_cut_noalloc serves them: the same cut as dc_cut for one grid, with
+// every scratch buffer carved from the fixed array below, which each GPU that
+// loads this library holds until the process exits.  In host code
+// `g_noalloc_scratch` only names a host-side stand-in for the symbol, never a
+// device address: the address the kernels get comes from
+// cudaGetSymbolAddress, once per device, with that device current.
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -1231,6 +1378,19 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   NoallocDevice& D = g_noalloc_dev[dev];
   dc_status rc = noalloc_setup(dev, D);
   if (rc) return rc;
+  // every check and query that can fail comes before the first queued copy:
+  // once work is on the stream, a failure waits for it before returning, so
+  // the lock is never released with work still running on the shared array
+  const int TB = 256;
+  const ExLayout Lf = ex_layout(p, q, 4), Ld = ex_layout(p, q, 8);
+  const int WPB = TB / 32;
+  if ((long long)Ld.total * WPB > D.smem_optin)
+    return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", p, q, Ld.total * WPB);
+  int occ = 0, occd = 0, occf = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB));
+  CK(cudaFuncSetAttribute(k_elem_frames, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frames_smem(npe)));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, k_elem_frames, FR_THREADS, frames_smem(npe)));
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* pp = D.scratch;
   auto take = [&](size_t bytes) { unsigned char* r = pp; pp += al256(bytes); return r; };
@@ -1265,7 +1425,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
     h.row_cnt = (int*)take(sizeof(int) * rows);
     h.row_x = (int*)take(sizeof(int) * rows * ROW_XCAP);
   }
-  int* d_bad = (int*)take(sizeof(int));
+  int* d_bad = (int*)take(sizeof(int) * 2);  // [0] non-finite node, [1] a node copy failed
   h.nbins_cap = nb;
   h.tol = tol;
   h.tol_f = float_up(tol);
@@ -1274,38 +1434,51 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   h.want_dist = dist_out ? 1 : 0;
   for (int a = 0; a < 3; ++a) { h.sbox_key[a] = ~0ULL; h.sbox_key[3 + a] = 0ULL; }
   long long off[4] = {0, n_faces, 0, n_elem};
-  // the array keeps the previous call's contents: reset what must start at zero
-  CK(cudaMemcpyAsync(d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
-  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
-  const int TB = 256;
-  k_elem_box<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(nodes, n_elem, npe, ebox, nullptr, nullptr, d_bad, nullptr);
+  // from here on a failure first drains what was queued
+  auto queued_fail = [&](const char* what, cudaError_t e) {
+    cudaStreamSynchronize(st);
+    return fail(DC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  };
+#define CKQ(call)                                 \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return queued_fail(#call, e_); \
+  } while (0)
+  // the array keeps the previous call's contents: the instance record and
+  // offsets are rewritten and the counters and the bad-node flag set to zero
+  // here; the hole map, bins and row tables are cleared by the kernels
+  // themselves (k_clear, k_tag, k_bin_scan), exactly as in a context's arena,
+  // which is also reused from cut to cut
+  CKQ(cudaMemcpyAsync(d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CKQ(cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
+  CKQ(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
+  CKQ(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
+  {
+    const int eb = frames_tile_elems(npe);
+    const long long grid = std::min<long long>((n_elem + eb - 1) / eb, (long long)D.n_sm * std::max(occf, 1));
+    k_elem_frames<<<(unsigned)grid, FR_THREADS, frames_smem(npe), st>>>(nodes, n_elem, npe, eb, ebox, nullptr,
+                                                                        nullptr, d_bad, nullptr, d_bad + 1);
+  }
   unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
   k_surface<<<dim3((unsigned)((n_faces + SURF_FPB - 1) / SURF_FPB), 1), TB, 0, st>>>(d_inst);
   k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);
   k_tag<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);
   k_bin_scan<<<1, 1024, 0, st>>>(d_inst);
-  CK(launch_rows(false, d_inst, d_off, 1, n_faces, n_faces * 2LL * q * q, st));
+  CKQ(launch_rows(false, d_inst, d_off, 1, n_faces, n_faces * 2LL * q * q, st));
   CandList cl{cand, (unsigned long long)n_elem, d_cnt};
   CandList rl{redo, (unsigned long long)n_elem, d_cnt + 2};
   CandList none{redo, 0, d_cnt + 2};
   k_classify<<<(unsigned)((n_elem + TB - 1) / TB), TB, 0, st>>>(d_inst, d_off + 2, 1, n_elem, cl, d_cnt);
-  const ExLayout Lf = ex_layout(p, q, 4), Ld = ex_layout(p, q, 8);
-  const int WPB = TB / 32;
-  if ((long long)Ld.total * WPB > D.smem_optin)
-    return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", p, q, Ld.total * WPB);
-  int occ = 0, occd = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB));
   k_exact<float><<<D.n_sm * std::max(occ, 1), TB, (size_t)Lf.total * WPB, st>>>(d_inst, cl, rl, p, q, d_cnt + 4);
   k_exact<double><<<D.n_sm * std::max(occd, 1), TB, (size_t)Ld.total * WPB, st>>>(d_inst, rl, none, p, q, d_cnt + 4);
-  CK(cudaGetLastError());
-  int bad = 0;
-  CK(cudaMemcpyAsync(&h, d_inst, sizeof(Inst), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (bad) return fail(DC_EINVAL, "an element node is NaN or infinite");
+  CKQ(cudaGetLastError());
+  int bad[2] = {0, 0};
+  CKQ(cudaMemcpyAsync(&h, d_inst, sizeof(Inst), cudaMemcpyDeviceToHost, st));
+  CKQ(cudaMemcpyAsync(bad, d_bad, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  CKQ(cudaStreamSynchronize(st));
+#undef CKQ
+  if (bad[1]) return fail(DC_EINTERNAL, "a bulk copy of element nodes did not complete");
+  if (bad[0]) return fail(DC_EINVAL, "an element node is NaN or infinite");
   if (h.err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
   if (h.err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");
   if (h.err & (ERR_ROUNDS | ERR_RECHECK)) return fail(DC_EINTERNAL, "exact test capacity exceeded (error bits 0x%x)", h.err);
@@ -1578,13 +1751,19 @@ dc_status dc_pc_create(int32_t device, int32_t p, int64_t n_elem, const double* 
       cudaMemcpyAsync(pc->tree, T.data(), sizeof(PcNode) * T.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return bail(fail(DC_ECUDA, "uploading the donor grid failed"));
   int* d_bad = nullptr;
-  if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
-  cudaMemsetAsync(d_bad, 0, sizeof(int), st);
-  k_elem_box<<<(unsigned)((n_elem + 255) / 256), 256, 0, st>>>(pc->nodes, (long long)n_elem, npe, pc->fbox, pc->loc,
-                                                                  pc->org, d_bad, nullptr);
-  const cudaError_t ke = cudaStreamSynchronize(st);
+  if (cudaMalloc(&d_bad, 2 * sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), st);
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t ke = launch_frames(pc->nodes, (long long)n_elem, npe, pc->fbox, pc->loc, pc->org, d_bad, nullptr,
+                                 std::max(n_sm, 1), st);
+  int hb[2] = {0, 0};
+  if (ke == cudaSuccess) ke = cudaMemcpyAsync(hb, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  const cudaError_t ks = cudaStreamSynchronize(st);
+  if (ke == cudaSuccess) ke = ks;
   cudaFree(d_bad);
   if (ke != cudaSuccess) return bail(fail(DC_ECUDA, "element frames failed: %s", cudaGetErrorString(ke)));
+  if (hb[1]) return bail(fail(DC_EINTERNAL, "a bulk copy of element nodes did not complete"));
   *out = pc;
   return DC_OK;
 }

@@ -40,10 +40,8 @@ enum : int {
 struct Inst {
   // background grid (resident)
   const double* nodes;   // [n_elem][(p+1)^3][3]
-  const float* eaabb;    // [n_elem][6] element node boxes, rounded outward
-  const float* eloc;     // [n_elem][3][(p+1)^3] node coordinates in the element frame
-                         // (x block, y block, z block), float; null in the allocation-free cut
-  const double* eorg;    // [n_elem][3] element frame origins (centre of the float box)
+  const float* eaabb;    // [n_elem][6] element node boxes, rounded outward (the element
+                         // frame's origin is the centre of this box)
   long long n_elem;
   int p;
   // cut surface
@@ -55,6 +53,9 @@ struct Inst {
   // outputs
   int8_t* flags;
   double* dist;            // may be null
+  float* dist32;           // may be null: each exact-test element's distance from
+                           // the FP32 bulk alone (signed as dist), before the FP64
+                           // re-solve; NaN where the FP32 stage computed none
   // scratch (per instance)
   double* surf;            // posed face nodes [n_faces][(q+1)^2][3]
   float* fbox;             // face node boxes [n_faces][6], float, rounded outward

@@ -208,7 +208,7 @@ constexpr int RCAP = 64;    // FP64 re-solve list
 struct ExLayout {
   int en, ebox, fn, fbx, flist, queue, rlist, rres, total;
 };
-__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline ExLayout ex_layout(int pmax, int qmax, int tsize) {
   int npe = (pmax + 1) * (pmax + 1) * (pmax + 1), nte = 12 * pmax * pmax;
   int npf = (qmax + 1) * (qmax + 1), ntf = 2 * qmax * qmax;
@@ -262,6 +262,7 @@ struct WarpState {
   unsigned fmask;                    // element faces whose triangles take part (bit f; 0x3f: all)
   double d_fringe;
   double dmin64;                     // FP64 minimum over re-solve entries already flushed
+  T U32;                             // smallest bulk-precision pair distance (no margin)
 };
 
 template <class T>
@@ -331,7 +332,7 @@ template <class T>
 __device__ __noinline__ void eval_batch(WarpCtx<T>& W, WarpState<T>& S, int n, int f, T sigma, T rho, ExCounters& cnt) {
   const unsigned FULL = 0xffffffffu;
   const int lane = S.lane;
-  T Uc = T(INFINITY), Lc = T(INFINITY);
+  T Uc = T(INFINITY), Lc = T(INFINITY), Ur = T(INFINITY);
   int te = 0, ts = 0;
   bool cert = false, zero = false;
   if (lane < n) {
@@ -358,9 +359,11 @@ __device__ __noinline__ void eval_batch(WarpCtx<T>& W, WarpState<T>& S, int n, i
     }
     Uc = U + sigma;
     Lc = L - sigma;
+    Ur = U;
     zero = (U == T(0));
   }
   cnt.bulk += (unsigned long long)n;
+  S.U32 = fmin(S.U32, warp_min(Ur));
   if (__any_sync(FULL, cert)) {
     S.fringe_done = true;
     S.d_fringe = 0.0;
@@ -764,6 +767,7 @@ __device__ bool process_element(WarpCtx<T>& W, WarpState<T>& S, ExCounters& cnt)
   S.fmask = 0x3fu;
   S.labeled = any_in != any_out;
   S.dmin64 = INFINITY;
+  S.U32 = T(INFINITY);
   if (any_in && any_out) {
     // nodes on both sides: the closed element boundary crosses the surface
     flag = DC_FRINGE_;
@@ -869,6 +873,12 @@ __device__ bool process_element(WarpCtx<T>& W, WarpState<T>& S, ExCounters& cnt)
   if (lane == 0) {
     in.flags[e] = flag;
     if (in.dist) in.dist[e] = dist;
+    if (in.dist32) {
+      // the bulk stage's own distance (FP32 instantiation only; an element
+      // settled by its node labels alone computed none)
+      const bool have = sizeof(T) == 4 && S.U32 < T(INFINITY);
+      in.dist32[e] = have ? (dist < 0.0 ? -(float)S.U32 : (float)S.U32) : __int_as_float(0x7fc00000);
+    }
   }
   if (flag == DC_FRINGE_) cnt.fringe++;
   else if (flag == DC_HOLE_) cnt.hole++;

@@ -1,0 +1,234 @@
+// dc_frames.cuh -- the sweep over every element node (the cold path of a
+// resident grid): element node boxes rounded outward and, when asked, the
+// element frame every exact test uses (origin at the centre of the float box,
+// node coordinates relative to it rounded to float, [e][x|y|z block][node]).
+//
+// The node array is the one place the whole grid is read ((p+1)^3 x 3 FP64 per
+// element, 170 MB at 64^3 Q2), so it is read as contiguous tiles: a block
+// takes `eb` consecutive elements at a time (eb * (p+1)^3 * 24 bytes, at most
+// 48 KB), one thread copies each tile into shared memory with a bulk
+// asynchronous copy (cp.async.bulk, completion counted on an mbarrier) while
+// the block works on the previous tile (two buffers), and the block writes its
+// boxes, origins and frame coordinates from shared memory in element order,
+// so every global access of the sweep is a contiguous span.  Tiles whose
+// global address or size is not a multiple of 16 bytes (a node array that is
+// not 16-byte aligned, the grid's last tile) are loaded by the threads with
+// plain coalesced loads instead.
+//
+// Every wait on the mbarrier is bounded: a wait that runs out sets *err, the
+// block waits (bounded again) for its own copies, and returns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <stdint.h>
+
+namespace dc {
+
+constexpr int FR_THREADS = 256;
+constexpr int FR_MAX_TILE_BYTES = 48 * 1024;
+constexpr unsigned FR_WAIT_LIMIT = 1u << 22;  // try_wait polls before a wait gives up
+
+// elements per tile: the largest power of two (<= 128) whose nodes fit 48 KB
+__host__ __device__ inline int frames_tile_elems(int npe) {
+  int eb = 128;
+  while (eb > 1 && (long long)eb * npe * 24 > FR_MAX_TILE_BYTES) eb >>= 1;
+  return eb;
+}
+
+// GB300 issues FP64 arithmetic at about 1/64 of its FP32 rate, so the box of
+// the nodes is taken on integer keys of the FP64 bit patterns: for finite
+// doubles the key order is the numeric order (negative values have their
+// magnitude bits flipped), and the key map is its own inverse.
+__device__ __forceinline__ long long fr_key(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
+
+__device__ __forceinline__ unsigned fr_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void fr_bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fr_smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one thread: expect `bytes` on the barrier and start the bulk copy
+__device__ __forceinline__ void fr_bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fr_smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          fr_smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(fr_smem_addr(bar))
+      : "memory");
+}
+
+// bounded wait for phase `parity` of the barrier; false if it never came
+__device__ __forceinline__ bool fr_bar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < FR_WAIT_LIMIT; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(fr_smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// grid: persistent blocks of FR_THREADS threads, dynamic shared memory
+// 2 * eb * npe * 24 bytes (two tile buffers).  loc/org may be null (boxes
+// only), ext_sum may be null.
+__global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __restrict__ nodes, long long n_elem,
+                                                            int npe, int eb, float* __restrict__ box,
+                                                            float* __restrict__ loc, double* __restrict__ org,
+                                                            int* __restrict__ bad, double* __restrict__ ext_sum,
+                                                            int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ double s_org[128][3];
+  __shared__ double s_ext[FR_THREADS / 32];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  const long long tile_doubles = (long long)eb * npe * 3;
+  double* const buf0 = reinterpret_cast<double*>(smem);
+  double* const buf1 = buf0 + tile_doubles;
+  const long long n_tiles = (n_elem + eb - 1) / eb;
+  const bool aligned = ((uintptr_t)nodes & 15) == 0;
+  // a tile goes by bulk copy when its address and size are 16-byte multiples
+  auto bulk_ok = [&](long long t) {
+    const long long ne = (t + 1) * eb <= n_elem ? eb : n_elem - t * eb;
+    return aligned && ((t * eb * npe * 24) & 15) == 0 && ((ne * npe * 24) & 15) == 0;
+  };
+  auto tile_elems = [&](long long t) { return (int)((t + 1) * eb <= n_elem ? eb : n_elem - t * eb); };
+  if (tid == 0) {
+    fr_bar_init(&bar[0]);
+    fr_bar_init(&bar[1]);
+    s_bad = 0;
+  }
+  if (tid < FR_THREADS / 32) s_ext[tid] = 0.0;
+  __syncthreads();
+  long long t = blockIdx.x;
+  unsigned phase = 0u;   // bit b: parity of buffer b's next phase
+  unsigned issued = 0u;  // bit b: buffer b has a bulk copy outstanding (thread 0's record)
+  bool failed = false;
+  if (t < n_tiles && tid == 0 && bulk_ok(t)) {
+    fr_bulk_load(buf0, nodes + t * tile_doubles, (unsigned)(tile_elems(t) * npe * 24), &bar[0]);
+    issued |= 1u;
+  }
+  // per element: T_E = FR_THREADS / eb threads (eb <= 128 so T_E >= 2)
+  const int te = FR_THREADS / eb;
+  double ext_acc = 0.0;
+  for (int k = 0; t < n_tiles; ++k, t += gridDim.x) {
+    const int b = k & 1;
+    const long long tn = t + gridDim.x;
+    if (tn < n_tiles && tid == 0 && bulk_ok(tn)) {
+      // the other buffer was released by the barrier at the end of the last round
+      fr_bulk_load(b ? buf0 : buf1, nodes + tn * tile_doubles, (unsigned)(tile_elems(tn) * npe * 24), &bar[b ^ 1]);
+      issued |= 1u << (b ^ 1);
+    }
+    const int ne = tile_elems(t);
+    double* tb = b ? buf1 : buf0;
+    if (bulk_ok(t)) {
+      if (fr_bar_wait(&bar[b], (phase >> b) & 1u)) {
+        phase ^= 1u << b;
+        issued &= ~(1u << b);
+      } else {
+        failed = true;  // phase and count stay: the clean-up waits for this copy
+      }
+    } else {
+      const double* src = nodes + t * tile_doubles;
+      for (long long j = tid; j < (long long)ne * npe * 3; j += FR_THREADS) tb[j] = src[j];
+    }
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    // boxes: thread group g (te threads) reduces element g's nodes, on the
+    // integer keys (a coordinate of magnitude 1e300 or more, or not finite,
+    // marks the grid bad)
+    const int g = tid / te, r = tid - g * te;
+    const long long big = __double_as_longlong(1e300);
+    long long klo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, khi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    bool nonfinite = false;
+    if (g < ne) {
+      const long long* x = reinterpret_cast<const long long*>(tb) + (long long)g * npe * 3;
+      for (int nd = r; nd < npe; nd += te)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const long long b = x[3 * nd + a];
+          nonfinite |= (b & 0x7fffffffffffffffLL) >= big;
+          const long long k = fr_key(b);
+          klo[a] = min(klo[a], k);
+          khi[a] = max(khi[a], k);
+        }
+    }
+    for (int s = 1; s < te; s <<= 1)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        klo[a] = min(klo[a], __shfl_xor_sync(0xffffffffu, klo[a], s));
+        khi[a] = max(khi[a], __shfl_xor_sync(0xffffffffu, khi[a], s));
+      }
+    if (nonfinite) s_bad = 1;
+    if (g < ne && r == 0) {
+      const long long e = t * eb + g;
+      double ext = 0.0;
+      double lo[3], hi[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = __longlong_as_double(fr_key(klo[a]));
+        hi[a] = __longlong_as_double(fr_key(khi[a]));
+      }
+      for (int a = 0; a < 3; ++a) {
+        const float bl = __double2float_rd(lo[a]), bh = __double2float_ru(hi[a]);
+        box[6 * e + a] = bl;
+        box[6 * e + 3 + a] = bh;
+        s_org[g][a] = 0.5 * ((double)bl + (double)bh);
+        ext = fmax(ext, hi[a] - lo[a]);
+      }
+      if (ext < 1e300) ext_acc += ext;
+    }
+    __syncthreads();
+    if (loc) {
+      // the tile's frame coordinates are one contiguous span of the output
+      const int per = 3 * npe;
+      float* out = loc + t * eb * (long long)per;
+      for (int j = tid; j < ne * per; j += FR_THREADS) {
+        const int el = j / per, rr = j - el * per, a = rr / npe, nd = rr - a * npe;
+        out[j] = (float)(tb[(long long)el * per + 3 * nd + a] - s_org[el][a]);
+      }
+      for (int j = tid; j < ne * 3; j += FR_THREADS) org[t * eb * 3 + j] = s_org[j / 3][j % 3];
+    }
+    __syncthreads();  // this buffer and s_org are free for the next tiles
+  }
+  if (failed) {
+    // a copy never completed: note it, let this block's own copies land
+    // (bounded), and leave
+    if (tid == 0) {
+      atomicOr(err, 1);
+      for (int b = 0; b < 2; ++b)
+        if ((issued >> b) & 1u) fr_bar_wait(&bar[b], (phase >> b) & 1u);  // at most one copy per buffer
+    }
+    return;
+  }
+  if (ext_sum) {
+    for (int s = 16; s; s >>= 1) ext_acc += __shfl_xor_sync(0xffffffffu, ext_acc, s);
+    if ((tid & 31) == 0) s_ext[tid >> 5] = ext_acc;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < FR_THREADS / 32; ++w) sum += s_ext[w];
+      if (sum > 0.0) atomicAdd(ext_sum, sum);
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && s_bad) atomicOr(bad, 1);
+}
+
+// dynamic shared memory of k_elem_frames for elements of npe nodes
+inline size_t frames_smem(int npe) { return (size_t)2 * frames_tile_elems(npe) * npe * 24; }
+
+}  // namespace dc

@@ -403,7 +403,11 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
       }
     }
     // pass 1: lane i < n1 owns kept face i (rank i); nearest corner in FP64
-    const double o[3] = {in.eorg[3 * e], in.eorg[3 * e + 1], in.eorg[3 * e + 2]};
+    // the element frame (origin at the centre of the float box), as the exact
+    // stage forms it
+    const float* gbx = in.eaabb + 6 * e;
+    const double o[3] = {0.5 * ((double)gbx[0] + (double)gbx[3]), 0.5 * ((double)gbx[1] + (double)gbx[4]),
+                         0.5 * ((double)gbx[2] + (double)gbx[5])};
     const int fid = id64;
     int corner = 0;
     {
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
     __syncwarp();
     // FP32 corner-triangle pairs, 12 per kept face, certified bounds per face
     {
-      const float* el = in.eloc + e * 3 * npe;
+      const double* xn = in.nodes + e * 3 * npe;
       for (int base = 0; base < 12 * n1; base += 32) {
         const int P = base + lane;
         const int i = P / 12;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(256, 2) k_heur_select(Inst* __restrict__ I, Ca
           float S = 0.f;
 #pragma unroll
           for (int v = 0; v < 3; ++v) {
-            a[v] = mkv(el[nd[v]], el[npe + nd[v]], el[2 * npe + nd[v]]);
+            a[v] = mkv((float)(xn[3 * nd[v]] - o[0]), (float)(xn[3 * nd[v] + 1] - o[1]), (float)(xn[3 * nd[v] + 2] - o[2]));
             const float* fc = &s_fc[wid][i][3 * tf[v]];
             b[v] = mkv(fc[0], fc[1], fc[2]);
             S = fmaxf(S, fmaxf(fmaxf(fabsf(a[v].x), fabsf(a[v].y)), fabsf(a[v].z)));

@@ -23,9 +23,12 @@
 // overflows); keeping that search and its shared scratch out of this kernel
 // leaves it a smaller code footprint and more of the SM's storage as L1.  The
 // element frame (origin at the centre of the element's float box, node
-// coordinates rounded to float) is the one the full search uses, computed once
-// per resident grid; FP64 arithmetic, slow on this GPU, is left to the face
-// conversions and the rare re-solves.
+// coordinates rounded to float) is the one the full search uses, formed for
+// each candidate from its FP64 nodes (candidates are a few percent of the grid:
+// forming frames for every element when the grid is created would cost the
+// sweep over the nodes more FP64 work than every cut's candidates together);
+// the rest of the FP64 arithmetic, slow on this GPU, is the face conversions
+// and the rare re-solves.
 #pragma once
 
 #include "dc_exact.cuh"
@@ -224,21 +227,26 @@ __device__ __noinline__ bool near_settle(const Inst& in, long long e, const doub
   return false;
 }
 
+// faces of one candidate tested together (their nodes are loaded at once)
+constexpr int NEAR_FB = 8;
+
 struct NearLayout {
-  int en, eb, fn, fb, ci, pq, ul, total;
+  int en, eb, fid, ffb, fn, fb, ci, pq, ul, total;
 };
-__host__ __device__ inline NearLayout near_layout(int pmax, int qmax) {
+__host__ __device__ constexpr NearLayout near_layout(int pmax, int qmax) {
   const int npe = (pmax + 1) * (pmax + 1) * (pmax + 1), nte = 12 * pmax * pmax;
   const int npf = (qmax + 1) * (qmax + 1), ntf = 2 * qmax * qmax;
-  NearLayout L;
+  NearLayout L{};
   int o = 0;
-  L.en = o; o = align16(o + 3 * npe * 4);   // element nodes, frame coordinates (x, y, z blocks)
-  L.eb = o; o = align16(o + 6 * nte * 4);   // element triangle boxes [6][nte]
-  L.fn = o; o = align16(o + 3 * npf * 4);   // face nodes, same frame
-  L.fb = o; o = align16(o + 6 * ntf * 4);   // face triangle boxes [6][ntf]
-  L.ci = o; o = align16(o + 32 * 4);        // near element triangles of a chunk
-  L.pq = o; o = align16(o + 64 * 4);        // queued pairs (te << 8 | ts)
-  L.ul = o; o = align16(o + NEAR_UCAP * 8); // undecided pairs (face, te | ts << 16)
+  L.en = o; o = align16(o + 3 * npe * 4);              // element nodes, frame coordinates (x, y, z blocks)
+  L.eb = o; o = align16(o + 6 * nte * 4);              // element triangle boxes [6][nte]
+  L.fid = o; o = align16(o + NEAR_FB * 4);             // faces of the batch
+  L.ffb = o; o = align16(o + NEAR_FB * 8 * 4);         // their boxes in the frame (lo, hi)
+  L.fn = o; o = align16(o + NEAR_FB * 3 * npf * 4);    // their nodes in the frame [face][x|y|z][node]
+  L.fb = o; o = align16(o + NEAR_FB * 6 * ntf * 4);    // their triangle boxes [face][6][ntf]
+  L.ci = o; o = align16(o + 32 * 4);                   // near (face, element triangle) of a chunk
+  L.pq = o; o = align16(o + 64 * 4);                   // queued pairs (face << 16 | te << 8 | ts)
+  L.ul = o; o = align16(o + NEAR_UCAP * 8);            // undecided pairs (face id, te | ts << 16)
   L.total = o;
   return L;
 }
@@ -246,15 +254,19 @@ __host__ __device__ inline NearLayout near_layout(int pmax, int qmax) {
 // bytes of shared scratch per warp of k_near_main (the full per-element search
 // runs in the exact kernels, with their own layout, so none is kept for it:
 // the smaller reservation leaves the SM's combined L1 / shared storage to L1)
-__host__ __device__ inline int near_region(int pmax, int qmax) { return near_layout(pmax, qmax).total; }
+__host__ __device__ constexpr int near_region(int pmax, int qmax) { return near_layout(pmax, qmax).total; }
 
 // at most 16 warps per block (4, 8 or 16 are launched; 128 registers per
 // thread either way)
 constexpr int NEAR_MAX_WARPS = 16;
 
+// P, Q > 0: every instance has element order P and face order Q (counts and
+// offsets known at compile time); P = Q = 0: any orders up to pmax, qmax.
+template <int P, int Q>
 __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     k_near_main(Inst* __restrict__ I, CandList cl, CandList full, NearBufs nb, int pmax, int qmax, int cpw,
                 unsigned long long* __restrict__ gcnt) {
+  constexpr bool FIXED = P > 0 && Q > 0;
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned char s_et[MAX_P][MAX_NTE][3], s_ft[MAX_Q][MAX_NTF][3];
@@ -263,8 +275,8 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   pdl_enter();
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const NearLayout Lo = near_layout(pmax, qmax);
-  unsigned char* ws = smem + (size_t)wid * near_region(pmax, qmax);
+  const NearLayout Lo = FIXED ? near_layout(P, Q) : near_layout(pmax, qmax);
+  unsigned char* ws = smem + (size_t)wid * Lo.total;
   unsigned long long n_fs = 0;
   // a candidate that needs the full per-element search (distances requested,
   // or no node labelled and not fringe) goes to the exact kernels' list;
@@ -279,13 +291,17 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   };
   float* en = reinterpret_cast<float*>(ws + Lo.en);
   float* eb = reinterpret_cast<float*>(ws + Lo.eb);
+  int* fid = reinterpret_cast<int*>(ws + Lo.fid);
+  float* ffb = reinterpret_cast<float*>(ws + Lo.ffb);
   float* fnl = reinterpret_cast<float*>(ws + Lo.fn);
   float* fb = reinterpret_cast<float*>(ws + Lo.fb);
   int* ci = reinterpret_cast<int*>(ws + Lo.ci);
   int* pq = reinterpret_cast<int*>(ws + Lo.pq);
   int2* ul = reinterpret_cast<int2*>(ws + Lo.ul);
   const unsigned long long ncand = ucount(cl.count, cl.cap);
-  unsigned long long n_fringe = 0, n_hole = 0, n_field = 0, n_faces = 0, n_pairs = 0, n_full = 0, n_re = 0;
+  // per-warp counts of one launch (32 bits suffice)
+  unsigned n_fringe = 0, n_hole = 0, n_field = 0, n_faces = 0, n_pairs = 0;
+  unsigned long long n_full = 0, n_re = 0;
   unsigned long long w = 0, wend = 0;
   while (true) {
     // candidates are taken from a shared cursor, cpw at a time: their costs
@@ -305,16 +321,19 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
       full_one(ent);
       continue;
     }
-    const int p = in.p, q = in.q;
+    const int p = FIXED ? P : in.p, q = FIXED ? Q : in.q;
     const int npe = (p + 1) * (p + 1) * (p + 1), nte = 12 * p * p, npf = (q + 1) * (q + 1), ntf = 2 * q * q;
     const float* gb = in.eaabb + 6 * e;
     float gbox[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) gbox[a] = gb[a];
-    const double eo[3] = {in.eorg[3 * e], in.eorg[3 * e + 1], in.eorg[3 * e + 2]};
+    // the element frame: origin at the centre of the float box, node
+    // coordinates relative to it rounded to float (the full search's frame)
+    const double eo[3] = {0.5 * ((double)gbox[0] + (double)gbox[3]), 0.5 * ((double)gbox[1] + (double)gbox[4]),
+                          0.5 * ((double)gbox[2] + (double)gbox[5])};
     // element nodes in the frame, and their hole-map labels (node = frame
     // origin + float local coordinate, as in the full search)
-    const float* el = in.eloc + e * 3 * npe;
+    const double* xn = in.nodes + e * npe * 3;
     float smax = 0.f;
     int lab_or = 0;
     {
@@ -326,9 +345,9 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
         const int nd = lane + 32 * r;
         lx[r] = ly[r] = lz[r] = 0.f;
         if (nd < npe) {
-          lx[r] = el[nd];
-          ly[r] = el[npe + nd];
-          lz[r] = el[2 * npe + nd];
+          lx[r] = (float)(xn[3 * nd] - eo[0]);
+          ly[r] = (float)(xn[3 * nd + 1] - eo[1]);
+          lz[r] = (float)(xn[3 * nd + 2] - eo[2]);
           en[nd] = lx[r];
           en[npe + nd] = ly[r];
           en[2 * npe + nd] = lz[r];
@@ -354,23 +373,23 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     bool have_eb = false;
     // element triangle boxes, once per element (when its first face is found)
     auto make_eb = [&]() {
-    __syncwarp();
-    for (int te = lane; te < nte; te += 32) {
-      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      __syncwarp();
+      for (int te = lane; te < nte; te += 32) {
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int nd = s_et[p - 1][te][c];
+        for (int c = 0; c < 3; ++c) {
+          const int nd = s_et[p - 1][te][c];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float v = en[a * npe + nd];
-          lo[a] = fminf(lo[a], v);
-          hi[a] = fmaxf(hi[a], v);
+          for (int a = 0; a < 3; ++a) {
+            const float v = en[a * npe + nd];
+            lo[a] = fminf(lo[a], v);
+            hi[a] = fmaxf(hi[a], v);
+          }
         }
-      }
 #pragma unroll
-      for (int a = 0; a < 3; ++a) { eb[a * nte + te] = lo[a]; eb[(3 + a) * nte + te] = hi[a]; }
-    }
-    __syncwarp();
+        for (int a = 0; a < 3; ++a) { eb[a * nte + te] = lo[a]; eb[(3 + a) * nte + te] = hi[a]; }
+      }
+      __syncwarp();
     };
     // faces whose boxes come within tol of the element box (each face sits in
     // the one bin of its box's low corner, hence the fext widening)
@@ -396,12 +415,161 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     const bool lvalid = lk < G;
     bool fringe = false;
     int nul = 0;  // undecided pairs held in ul
+    int nbf = 0;  // faces gathered into the batch
+    int nq = 0;   // queued pairs
     // the held pairs: FP32 bounds (the compact form of the triangle test),
     // then FP64 (warp-parallel) for what they cannot clear
     auto settle = [&]() {
       __syncwarp();
       if (near_settle(in, e, eo, en, ul, nul, s_et, s_ft, lane, n_full, n_re)) fringe = true;
       nul = 0;
+      __syncwarp();
+    };
+    // the queued pairs, 32 lanes at a time: separation, then crossings; the
+    // rest are listed undecided
+    auto drain = [&](int n) {
+      bool need = false, crossed = false;
+      int fi = 0, te = 0, ts = 0;
+      V3<float> A[3], B[3];
+      float S = 0.f;
+      if (lane < n) {
+        const int code = pq[lane];
+        fi = code >> 16;
+        te = (code >> 8) & 255;
+        ts = code & 255;
+        const float* fx = fnl + fi * 3 * npf;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int ni = s_et[p - 1][te][c], nj = s_ft[q - 1][ts][c];
+          A[c] = mkv(en[ni], en[npe + ni], en[2 * npe + ni]);
+          B[c] = mkv(fx[nj], fx[npf + nj], fx[2 * npf + nj]);
+          S = fmaxf(S, fmaxf(fmaxf(fabsf(A[c].x), fabsf(A[c].y)), fabsf(A[c].z)));
+          S = fmaxf(S, fmaxf(fmaxf(fabsf(B[c].x), fabsf(B[c].y)), fabsf(B[c].z)));
+        }
+        need = !near_separated(A, B, S, tolf);
+      }
+      n_pairs += (unsigned)n;
+      if (need) crossed = near_cross(A, B, S);
+      if (__any_sync(FULL, crossed)) {
+        fringe = true;
+      } else {
+        const unsigned um = __ballot_sync(FULL, need);
+        if (um) {
+          if (nul + __popc(um) > 32) settle();
+          if (!fringe) {
+            if (need) ul[nul + __popc(um & ((1u << lane) - 1u))] = make_int2(fid[fi], te | (ts << 16));
+            nul += __popc(um);
+          }
+        }
+      }
+      __syncwarp();
+      const int rem = nq - n;
+      const int v = lane < rem ? pq[n + lane] : 0;
+      __syncwarp();
+      if (lane < rem) pq[lane] = v;
+      nq = rem;
+      __syncwarp();
+    };
+    // the faces of the batch together: nodes into the frame (every node load
+    // of the batch in flight at once), frame boxes and rounding bounds,
+    // triangle boxes, then the (face, element triangle) pairs whose boxes come
+    // within tol and their triangle pairs
+    auto run_batch = [&]() {
+      if (!have_eb) { make_eb(); have_eb = true; }
+      n_faces += (unsigned)nbf;
+      const int per = 3 * npf;
+      // nodes of every face of the batch into the frame; the loads of all of
+      // them are issued before any is used
+      float smx = 0.f;
+#pragma unroll
+      for (int fi = 0; fi < NEAR_FB; ++fi) {
+        if (fi < nbf) {
+          const double* src = in.surf + (long long)fid[fi] * per;
+          for (int r = lane; r < per; r += 32) {
+            const int nd = r / 3, a = r - nd * 3;
+            const float v = (float)(src[r] - eo[a]);
+            fnl[fi * per + a * npf + nd] = v;
+            smx = fmaxf(smx, fabsf(v));
+          }
+        }
+      }
+      // one rounding bound for the batch: the largest coordinate of the
+      // element and of any of its faces (a bound for each face, as a
+      // face's own largest coordinate is never above it)
+      const float sigma = (float)C_SIGMA * Eps<float>::u * fmaxf(Se, warp_max(smx));
+      if (lane < nbf) {
+        // the face box in the frame, from its outward float box: the two
+        // subtractions and the float origin are within 4u of their operands,
+        // which the slack covers (it only widens the box)
+        const float* fbx = in.fbox + 6 * (long long)fid[lane];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float o = (float)eo[a], l = fbx[a], h = fbx[3 + a];
+          const float sl = 4.0f * 5.9604645e-8f * (fabsf(l) + fabsf(h) + 2.0f * fabsf(o));
+          ffb[lane * 8 + a] = (l - o) - sl;
+          ffb[lane * 8 + 3 + a] = (h - o) + sl;
+        }
+      }
+      __syncwarp();
+      for (int k = lane; k < nbf * ntf; k += 32) {
+        const int fi = k / ntf, ts = k - fi * ntf;
+        const float* fx = fnl + fi * per;
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int nd = s_ft[q - 1][ts][c];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float v = fx[a * npf + nd];
+            lo[a] = fminf(lo[a], v);
+            hi[a] = fmaxf(hi[a], v);
+          }
+        }
+        float* fbo = fb + fi * 6 * ntf;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { fbo[a * ntf + ts] = lo[a]; fbo[(3 + a) * ntf + ts] = hi[a]; }
+      }
+      __syncwarp();
+      for (int base = 0; base < nbf * nte && !fringe; base += 32) {
+        // (face, element triangle) of this chunk whose boxes come within tol, compacted
+        const int k = base + lane;
+        bool near = false;
+        int code = 0;
+        if (k < nbf * nte) {
+          const int fi = k / nte, te = k - fi * nte;
+          const float* fr = ffb + fi * 8;
+          near = box_dist<float>(eb[te], eb[nte + te], eb[2 * nte + te], eb[3 * nte + te], eb[4 * nte + te],
+                                 eb[5 * nte + te], fr[0], fr[1], fr[2], fr[3], fr[4], fr[5]) - sigma <= tolf;
+          code = (fi << 16) | te;
+        }
+        const unsigned em = __ballot_sync(FULL, near);
+        if (near) ci[__popc(em & ((1u << lane) - 1u))] = code;
+        const int nnear = __popc(em);
+        __syncwarp();
+        for (int g0 = 0; g0 < nnear && !fringe; g0 += G) {
+          const int kk2 = g0 + lk;
+          bool keep2 = false;
+          int c2 = 0;
+          if (lvalid && kk2 < nnear) {
+            c2 = ci[kk2];
+            const int fi = c2 >> 16, tk = c2 & 0xffff;
+            const float* fbo = fb + fi * 6 * ntf;
+            keep2 = box_dist<float>(eb[tk], eb[nte + tk], eb[2 * nte + tk], eb[3 * nte + tk], eb[4 * nte + tk],
+                                    eb[5 * nte + tk], fbo[lts], fbo[ntf + lts], fbo[2 * ntf + lts],
+                                    fbo[3 * ntf + lts], fbo[4 * ntf + lts], fbo[5 * ntf + lts]) - sigma <= tolf;
+          }
+          const unsigned m2 = __ballot_sync(FULL, keep2);
+          if (keep2)
+            pq[nq + __popc(m2 & ((1u << lane) - 1u))] = ((c2 >> 16) << 16) | ((c2 & 0xffff) << 8) | lts;
+          nq += __popc(m2);
+          __syncwarp();
+          if (nq >= 32) drain(32);
+        }
+        __syncwarp();
+      }
+      if (!fringe && nq > 0) drain(nq);
+      nq = 0;
+      nbf = 0;
       __syncwarp();
     };
     for (int cb = 0; cb < nbins && !fringe; cb += 32) {
@@ -445,135 +613,24 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
           lb -= 8.0f * 5.9604645e-8f * fmaxf(gmax, fm);  // rounding of the float box distance
           keep = lb <= tolf;
         }
+        // the kept faces join the batch in lane order; a full batch is tested
         unsigned fm_ = __ballot_sync(FULL, keep);
         while (fm_ && !fringe) {
-          // one face: nodes into the frame, triangle boxes, pairs
-          const int srcl = __ffs(fm_) - 1;
-          fm_ &= fm_ - 1;
-          const int fc = __shfl_sync(FULL, f, srcl);
-          n_faces++;
-          if (!have_eb) { make_eb(); have_eb = true; }
-          const double* fsrcp = in.surf + (long long)fc * npf * 3;
-          float sf = 0.f;
-          for (int kq = lane; kq < 3 * npf; kq += 32) {
-            const int nd = kq / 3, a = kq - nd * 3;
-            const float v = (float)(fsrcp[kq] - eo[a]);
-            fnl[a * npf + nd] = v;
-            sf = fmaxf(sf, fabsf(v));
+          const int take = min(__popc(fm_), NEAR_FB - nbf);
+          unsigned sel = 0, mm = fm_;
+          for (int i = 0; i < take; ++i) {
+            sel |= mm & (0u - mm);
+            mm &= mm - 1u;
           }
-          sf = warp_max(sf);
-          const float sigma = (float)C_SIGMA * Eps<float>::u * fmaxf(Se, sf);
+          if ((sel >> lane) & 1u) fid[nbf + __popc(sel & ((1u << lane) - 1u))] = f;
+          fm_ &= ~sel;
+          nbf += take;
           __syncwarp();
-          if (lane < ntf) {
-            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const int nd = s_ft[q - 1][lane][c];
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                const float v = fnl[a * npf + nd];
-                lo[a] = fminf(lo[a], v);
-                hi[a] = fmaxf(hi[a], v);
-              }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) { fb[a * ntf + lane] = lo[a]; fb[(3 + a) * ntf + lane] = hi[a]; }
-          }
-          // the face box in the frame, from its outward float box: the two
-          // subtractions and the float origin are within 4u of their operands,
-          // which the slack covers (it only widens the box)
-          float flo[3], fhi[3];
-          {
-            const float* fbx = in.fbox + 6 * (long long)fc;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float o = (float)eo[a], l = fbx[a], h = fbx[3 + a];
-              const float sl = 4.0f * 5.9604645e-8f * (fabsf(l) + fabsf(h) + 2.0f * fabsf(o));
-              flo[a] = (l - o) - sl;
-              fhi[a] = (h - o) + sl;
-            }
-          }
-          __syncwarp();
-          float my[6];
-#pragma unroll
-          for (int a = 0; a < 6; ++a) my[a] = fb[a * ntf + (lvalid ? lts : 0)];
-          int nq = 0;
-          // the queued pairs, 32 lanes at a time: separation, then crossings;
-          // the rest are listed undecided
-          auto drain = [&](int n) {
-            bool need = false, crossed = false;
-            int te = 0, ts = 0;
-            V3<float> A[3], B[3];
-            float S = 0.f;
-            if (lane < n) {
-              const int code = pq[lane];
-              te = code >> 8;
-              ts = code & 255;
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const int ni = s_et[p - 1][te][c], nj = s_ft[q - 1][ts][c];
-                A[c] = mkv(en[ni], en[npe + ni], en[2 * npe + ni]);
-                B[c] = mkv(fnl[nj], fnl[npf + nj], fnl[2 * npf + nj]);
-                S = fmaxf(S, fmaxf(fmaxf(fabsf(A[c].x), fabsf(A[c].y)), fabsf(A[c].z)));
-                S = fmaxf(S, fmaxf(fmaxf(fabsf(B[c].x), fabsf(B[c].y)), fabsf(B[c].z)));
-              }
-              need = !near_separated(A, B, S, tolf);
-            }
-            n_pairs += (unsigned long long)n;
-            if (need) crossed = near_cross(A, B, S);
-            if (__any_sync(FULL, crossed)) {
-              fringe = true;
-            } else {
-              const unsigned um = __ballot_sync(FULL, need);
-              if (um) {
-                if (nul + __popc(um) > 32) settle();
-                if (!fringe) {
-                  if (need) ul[nul + __popc(um & ((1u << lane) - 1u))] = make_int2(fc, te | (ts << 16));
-                  nul += __popc(um);
-                }
-              }
-            }
-            __syncwarp();
-            const int rem = nq - n;
-            const int v = lane < rem ? pq[n + lane] : 0;
-            __syncwarp();
-            if (lane < rem) pq[lane] = v;
-            nq = rem;
-            __syncwarp();
-          };
-          for (int tb = 0; tb < nte && !fringe; tb += 32) {
-            // element triangles of this chunk near the face box, compacted
-            const int te = tb + lane;
-            bool near = false;
-            if (te < nte)
-              near = box_dist<float>(eb[te], eb[nte + te], eb[2 * nte + te], eb[3 * nte + te], eb[4 * nte + te],
-                                     eb[5 * nte + te], flo[0], flo[1], flo[2], fhi[0], fhi[1], fhi[2]) - sigma <= tolf;
-            const unsigned em = __ballot_sync(FULL, near);
-            if (near) ci[__popc(em & ((1u << lane) - 1u))] = te;
-            const int nnear = __popc(em);
-            __syncwarp();
-            for (int g0 = 0; g0 < nnear && !fringe; g0 += G) {
-              const int kk2 = g0 + lk;
-              bool keep2 = false;
-              int tk = 0;
-              if (lvalid && kk2 < nnear) {
-                tk = ci[kk2];
-                keep2 = box_dist<float>(eb[tk], eb[nte + tk], eb[2 * nte + tk], eb[3 * nte + tk], eb[4 * nte + tk],
-                                        eb[5 * nte + tk], my[0], my[1], my[2], my[3], my[4], my[5]) - sigma <= tolf;
-              }
-              const unsigned m2 = __ballot_sync(FULL, keep2);
-              if (keep2) pq[nq + __popc(m2 & ((1u << lane) - 1u))] = (tk << 8) | lts;
-              nq += __popc(m2);
-              __syncwarp();
-              if (nq >= 32) drain(32);
-            }
-            __syncwarp();
-          }
-          if (!fringe && nq > 0) drain(nq);
-          __syncwarp();
+          if (nbf == NEAR_FB) run_batch();
         }
       }
     }
+    if (!fringe && nbf > 0) run_batch();
     if (!fringe && nul > 0) settle();
     if (lane == 0) {
       if (fringe) {
@@ -592,14 +649,14 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   if (lane == 0) {
     if (n_fs) atomicAdd(&nb.cnt[3], n_fs);
     if (n_fringe | n_hole | n_field) {
-      atomicAdd(&gcnt[3], n_fringe);
-      atomicAdd(&gcnt[4], n_hole);
-      atomicAdd(&gcnt[5], n_field);
+      atomicAdd(&gcnt[3], (unsigned long long)n_fringe);
+      atomicAdd(&gcnt[4], (unsigned long long)n_hole);
+      atomicAdd(&gcnt[5], (unsigned long long)n_field);
     }
     if (n_faces) {
-      atomicAdd(&nb.cnt[0], n_faces);
-      atomicAdd(&gcnt[0], n_faces);
-      atomicAdd(&gcnt[1], n_pairs);
+      atomicAdd(&nb.cnt[0], (unsigned long long)n_faces);
+      atomicAdd(&gcnt[0], (unsigned long long)n_faces);
+      atomicAdd(&gcnt[1], (unsigned long long)n_pairs);
       atomicAdd(&nb.cnt[5], n_full);
       atomicAdd(&gcnt[2], n_re);
     }

@@ -576,6 +576,7 @@ __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const lo
       hole = flag == DC_HOLE_;
       in.flags[e] = flag;
       if (in.dist) in.dist[e] = (flag == DC_HOLE_) ? -HUGE_VAL : HUGE_VAL;
+      if (in.dist32) in.dist32[e] = (flag == DC_HOLE_) ? -INFINITY : INFINITY;
     }
   }
   const unsigned hm = __ballot_sync(FULL, hole);

@@ -1,4 +1,4 @@
-// flopcount.cu -- counts the arithmetic of one triangle-triangle evaluation
+// kernel_flops.cu -- counts the arithmetic of the kernels' triangle-triangle routine
 // (the per-unit figure of the exact-test roofline).
 //
 // The same tritri template the kernels use is instantiated on the host with a
@@ -10,7 +10,7 @@
 #include <cmath>
 #include <cstdio>
 
-#include "dc_exact.cuh"
+#include "dc_exact.cuh"  // from paper_1711_07663_gb300/csrc (-I)
 
 namespace fc {
 long long g_ops = 0;

@@ -51,9 +51,10 @@ def test_struct_layouts_match_header(tmp_path):
         "int main(void){\n"
         "S(dc_mesh_desc); F(dc_mesh_desc,p); F(dc_mesh_desc,n_elem); F(dc_mesh_desc,nodes); F(dc_mesh_desc,nodes_on_device);\n"
         "S(dc_config); F(dc_config,device); F(dc_config,precision); F(dc_config,mem_budget_bytes); F(dc_config,tol);\n"
-        "F(dc_config,holemap_cells); F(dc_config,bin_cubes); F(dc_config,max_inflight); F(dc_config,profile);\n"
+        "F(dc_config,holemap_cells); F(dc_config,bin_cubes); F(dc_config,max_inflight); F(dc_config,profile); F(dc_config,reserve_faces);\n"
         "S(dc_request); F(dc_request,q); F(dc_request,n_faces); F(dc_request,face_nodes); F(dc_request,pose);\n"
         "F(dc_request,flags_out); F(dc_request,dist_out); F(dc_request,on_device); F(dc_request,async); F(dc_request,stream);\n"
+        "F(dc_request,fp32_dist_out);\n"
         "S(dc_stats); F(dc_stats,holemap_rows_undecided); F(dc_stats,ms_surface); F(dc_stats,ms_total);\n"
         "S(dc_tuning); F(dc_tuning,cubes_per_edge); F(dc_tuning,bin_cubes); F(dc_tuning,warps_per_cta);\n"
         "F(dc_tuning,cands_per_warp); F(dc_tuning,ms);\n"

@@ -4,8 +4,13 @@ Flags must be bit-identical.  Distances: elements that reach the exact test
 must agree with the oracle within 1e-12 * max(|d|, h); elements decided by
 the hole map report -inf (hole) / +inf (field) and the oracle must agree on
 their side.  Sizes span several warps / bins / hole-map runs with ragged
-tails; the full 262,144-element workload is checked on sampled elements.
+tails; the full 262,144-element benchmark workload is checked on every
+element against the oracle's stored cut (tests/golden/scale64_cut.npz, written
+by tests/golden/scale64_cut.py, which calls only the oracle).
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
@@ -162,24 +167,101 @@ def test_precisions_agree_and_repeat_bit_identically():
     assert s1["pairs_recheck"] < s1["pairs_bulk"]
 
 
-def test_full_scale_dimpled_64cube_sampled():
+GOLDEN64 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "scale64_cut.npz")
+
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+@pytest.mark.parametrize("form", ["flags_only_bench_shape", "flags_only_default_shape", "fp32_recheck_dist",
+                                  "fp64_dist"])
+def test_full_scale_dimpled_64cube_every_element(form):
     """The 262,144-element scale workload (64^3 Q2, sinusoidal curving, dimpled
-    sphere of 6144 Q2 faces) in the benchmark's launch configuration; the oracle
-    re-computes a seeded sample of elements one by one (all near-surface
-    elements of a slab plus uniform picks)."""
+    sphere of 6144 Q2 faces), every element against the oracle's stored cut:
+    the flags-only form the benchmark times (its autotuned launch shape, 16
+    warps per block, and the default shape), and both distance forms (FP32 bulk
+    with FP64 re-solve, all FP64) with their distances."""
     c = W.dimpled_sphere_case()
-    f, d, st = gpu_cut(c.p, c.nodes, c.q, c.faces)
-    g = np.random.default_rng(0)
-    near = np.nonzero(np.isfinite(d))[0]
-    ids = np.unique(np.concatenate([g.choice(near, size=min(600, near.size), replace=False),
-                                    g.choice(c.n_elem, size=300, replace=False)]))
-    rf, rd, _, rst = O.cut(c.p, c.nodes, c.q, c.faces, ids=ids)
-    assert rst["undecidable"] == 0
-    check(f[ids], d[ids], rf, rd, 4.0 / c.n)
-    # properties that hold everywhere: fringe separates hole from field
-    G = f.reshape(c.n, c.n, c.n)
-    for ax in range(3):
-        a = np.moveaxis(G, ax, 0)
-        pairs = set(zip(a[:-1].ravel().tolist(), a[1:].ravel().tolist()))
-        assert (O.HOLE, O.FIELD) not in pairs and (O.FIELD, O.HOLE) not in pairs
-    assert st["n_candidates"] == int(np.isfinite(d).sum())
+    G = np.load(GOLDEN64)
+    assert str(G["nodes_sha256"]) == _sha(c.nodes) and str(G["faces_sha256"]) == _sha(c.faces), \
+        "the generated workload differs from the one the stored cut was computed on"
+    assert int(G["undecidable"]) == 0
+    ref_f = G["flags"]
+    h = 4.0 / c.n
+    dev = torch.device("cuda:0")
+    tn = torch.from_numpy(c.nodes).to(dev)
+    tf = torch.from_numpy(c.faces).to(dev)
+    flags = torch.full((c.n_elem,), 7, dtype=torch.int8, device=dev)
+    dist = None
+    prec = dc.DC_FP64 if form == "fp64_dist" else dc.DC_FP32_RECHECK
+    with dc.Context([(c.p, tn)], precision=prec) as ctx:
+        if form == "flags_only_bench_shape":
+            ctx.set_tuning(warps_per_cta=16, cands_per_warp=1)
+        if form.endswith("_dist"):
+            dist = torch.full((c.n_elem,), np.nan, dtype=torch.float64, device=dev)
+        ctx.cut(0, c.q, tf, flags, dist)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+    f = flags.cpu().numpy()
+    bad = np.nonzero(f != ref_f)[0]
+    assert bad.size == 0, f"{bad.size} flag mismatches, first {bad[:8]}: gpu {f[bad[:8]]} oracle {ref_f[bad[:8]]}"
+    if dist is None:
+        return
+    d = dist.cpu().numpy()
+    assert not np.any(np.isnan(d))
+    fin = np.nonzero(np.isfinite(d))[0]
+    assert st["n_candidates"] == fin.size
+    ids, rd = G["dist_ids"].astype(np.int64), G["dist"]
+    pos = np.searchsorted(ids, fin)
+    covered = (pos < ids.size) & (ids[np.minimum(pos, ids.size - 1)] == fin)
+    assert covered.all(), f"{int((~covered).sum())} exact-test elements lie beyond the stored band"
+    want = rd[pos]
+    err = np.abs(d[fin] - want)
+    assert np.all(err <= 1e-12 * np.maximum(np.abs(want), h)), f"max dist error {err.max():.3e}"
+    # the hole map's elements: never fringe, side by the sign
+    inf = ~np.isfinite(d)
+    assert np.all(ref_f[inf] != O.FRINGE)
+    assert np.array_equal(np.where(d[inf] > 0, O.FIELD, O.HOLE).astype(np.int8), ref_f[inf])
+
+
+def test_fp32_stage_distances_are_reported_within_their_rounding_bound():
+    """fp32_dist_out: the FP32 bulk's own distance of every exact-test element
+    (before any FP64 re-solve) lies within the FP32 rounding bound of the
+    final FP64 distance; hole-map elements get +-inf, elements the FP32 stage
+    never measured NaN; the output is refused without dist_out or in the
+    DC_FP64 precision."""
+    c = W.dimpled_sphere_case(n=20, p=2, m=10, q=2, n_dimples=120, seed=8)
+    dev = torch.device("cuda:0")
+    tn = torch.from_numpy(c.nodes).to(dev)
+    tf = torch.from_numpy(c.faces).to(dev)
+    h = 4.0 / c.n
+    f = torch.empty(c.n_elem, dtype=torch.int8, device=dev)
+    d = torch.empty(c.n_elem, dtype=torch.float64, device=dev)
+    d32 = torch.full((c.n_elem,), 7.0, dtype=torch.float32, device=dev)
+    with dc.Context([(c.p, tn)], precision=dc.DC_FP32_RECHECK) as ctx:
+        ctx.cut(0, c.q, tf, f, d, fp32_dist_out=d32)
+        with pytest.raises(dc.DirectCutError) as ei:
+            ctx.cut(0, c.q, tf, f, None, fp32_dist_out=d32)
+        assert ei.value.status == dc.DC_EINVAL
+        # host outputs take the same path through the arena's staging
+        fh = np.empty(c.n_elem, dtype=np.int8)
+        dh = np.empty(c.n_elem, dtype=np.float64)
+        eh = np.full(c.n_elem, 7.0, dtype=np.float32)
+        ctx.cut(0, c.q, c.faces, fh, dh, fp32_dist_out=eh)
+    with dc.Context([(c.p, tn)], precision=dc.DC_FP64) as ctx:
+        with pytest.raises(dc.DirectCutError) as ei:
+            ctx.cut(0, c.q, tf, f, d, fp32_dist_out=d32)
+        assert ei.value.status == dc.DC_EINVAL
+    dd, ee = d.cpu().numpy(), d32.cpu().numpy()
+    assert np.array_equal(ee, eh, equal_nan=True) and np.array_equal(dd, dh)
+    fin = np.isfinite(dd)
+    assert not np.any(ee == 7.0)
+    assert np.array_equal(np.isinf(ee), ~fin)
+    assert np.array_equal(np.sign(ee[~fin]), np.sign(dd[~fin]))
+    have = fin & ~np.isnan(ee)
+    assert have.sum() > 50
+    # the same side, and within 64 u S (S < 2 h: element and nearby faces in
+    # the element's frame)
+    assert np.array_equal(np.signbit(ee[have]), np.signbit(dd[have]))
+    assert np.all(np.abs(ee[have].astype(np.float64) - dd[have]) <= 64 * 2.0 ** -24 * 2 * h)

@@ -162,18 +162,25 @@ def hex_lattice(n: int, p: int, lo: float = -2.0, hi: float = 2.0) -> np.ndarray
     return np.stack([x, y, z], axis=-1).reshape(m, m, m, 3)
 
 
+def gather_index(n: int, p: int) -> np.ndarray:
+    """Flat lattice index [n^3][(p+1)^3] (int64) of every element node: the
+    nodes of element ex + n*(ey + n*ez) are lattice.reshape(-1, 3)[index[e]]."""
+    e = np.arange(n, dtype=np.int64)
+    l = np.arange(p + 1, dtype=np.int64)
+    ez, ey, ex = np.meshgrid(e, e, e, indexing="ij")
+    lk, lj, li = np.meshgrid(l, l, l, indexing="ij")
+    m = n * p + 1
+    X = (ex.reshape(-1, 1) * p + li.reshape(1, -1))
+    Y = (ey.reshape(-1, 1) * p + lj.reshape(1, -1))
+    Z = (ez.reshape(-1, 1) * p + lk.reshape(1, -1))
+    return np.ascontiguousarray((Z * m + Y) * m + X)
+
+
 def gather_elements(lattice: np.ndarray, n: int, p: int) -> np.ndarray:
     """Per-element node arrays [n^3][(p+1)^3][3] gathered from the lattice, so
     nodes shared between elements are bit-identical.  Element (ex,ey,ez) is
     number ex + n*(ey + n*ez)."""
-    e = np.arange(n)
-    l = np.arange(p + 1)
-    ez, ey, ex = np.meshgrid(e, e, e, indexing="ij")
-    lk, lj, li = np.meshgrid(l, l, l, indexing="ij")
-    X = (ex.reshape(-1, 1) * p + li.reshape(1, -1))
-    Y = (ey.reshape(-1, 1) * p + lj.reshape(1, -1))
-    Z = (ez.reshape(-1, 1) * p + lk.reshape(1, -1))
-    return np.ascontiguousarray(lattice[Z, Y, X])
+    return np.ascontiguousarray(lattice.reshape(-1, lattice.shape[-1])[gather_index(n, p)])
 
 
 def jitter_lattice(lattice: np.ndarray, amp: float, g: np.random.Generator) -> np.ndarray:
@@ -343,6 +350,7 @@ class CutCase:
     q: int
     faces: np.ndarray          # [n_faces][(q+1)^2][3]
     pose: np.ndarray | None = None  # 3x4 [R|t] applied to faces, or None
+    centre: np.ndarray | None = None  # centre of the (sphere-like) surface, before the pose
 
     @property
     def n_elem(self) -> int:
@@ -363,7 +371,7 @@ def sphere_in_box(n: int = 16, p: int = 2, m: int = 8, q: int = 2, seed: int = 1
     centre = g.uniform(-offset, offset, size=3)
     nodes = background(n, p, jitter=jitter, seed=seed + 1000)
     faces = cubed_sphere(m, q, radius=radius, centre=centre)
-    return CutCase(f"sphere{n}^3Q{p}_m{m}q{q}", p, n, nodes, q, faces)
+    return CutCase(f"sphere{n}^3Q{p}_m{m}q{q}", p, n, nodes, q, faces, centre=centre)
 
 
 def dimpled_sphere_case(n: int = 64, p: int = 2, m: int = 32, q: int = 2, seed: int = 2, n_dimples: int = 336,
@@ -379,7 +387,7 @@ def dimpled_sphere_case(n: int = 64, p: int = 2, m: int = 32, q: int = 2, seed: 
     centres = fibonacci_sphere(n_dimples, rot)
     nodes = background(n, p, sinusoid=sinusoid)
     faces = cubed_sphere(m, q, radius=1.0, centre=centre, dimples=centres)
-    return CutCase(f"dimpled{n}^3Q{p}_m{m}q{q}", p, n, nodes, q, faces)
+    return CutCase(f"dimpled{n}^3Q{p}_m{m}q{q}", p, n, nodes, q, faces, centre=centre)
 
 
 def batch_cases(count: int = 256, seed: int = 3, n_range=(8, 40), m_choices=(8, 16, 24, 32), p: int = 2,
@@ -400,7 +408,7 @@ def batch_cases(count: int = 256, seed: int = 3, n_range=(8, 40), m_choices=(8, 
             base_faces[m] = cubed_sphere(m, q)
         pose = np.concatenate([rot, off.reshape(3, 1)], axis=1)
         nodes = background(n, p, jitter=jitter, seed=seed * 100003 + i)
-        out.append(CutCase(f"batch{i}_{n}^3_m{m}", p, n, nodes, q, base_faces[m], pose))
+        out.append(CutCase(f"batch{i}_{n}^3_m{m}", p, n, nodes, q, base_faces[m], pose, np.zeros(3)))
     return out
 
 

@@ -205,6 +205,7 @@ struct Slot {
 };
 
 constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters,
+                          // [22] the prep kernel's barrier count (low half) and time-out flag,
                           // [11] near faces tested, [12] holes decided by the hole map,
                           // [14] near full searches, [16] near pairs given the
                           // full FP32 test, [17] truncating variant: FP64 key
@@ -475,25 +476,38 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
   long long* d_off = P.d_off;
   unsigned long long *cand = P.cand, *redo = P.redo, *d_cnt = P.d_cnt;
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
-  const long long* foff = d_off;
-  const long long* eoff = d_off + n + 1;
   const bool prof = P.prof != 0;
   if (prof) CK(record(s.ev[0], st, capturing));
 
   const int TB = 256;
-  unsigned gf = (unsigned)((nf_total + TB - 1) / TB);
-  CK(launch_k(false, k_surface, dim3((unsigned)((P.max_f + SURF_FPB - 1) / SURF_FPB), n), dim3(TB), 0, st, d_inst));
-  CK(launch_k(true, k_clear, dim3(64, n), dim3(TB), 0, st, d_inst));
-  CK(launch_k(true, k_tag, dim3(gf), dim3(TB), 0, st, d_inst, foff, n, nf_total));
-  CK(launch_k(true, k_bin_scan, dim3(n), dim3(1024), 0, st, d_inst));
-  if (prof) CK(record(s.ev[1], st, capturing));
-  CK(launch_rows(true, d_inst, foff, n, nf_total, max_tri, st));
-  if (prof) CK(record(s.ev[2], st, capturing));
+  (void)max_tri;
   CandList cl{cand, (unsigned long long)ne_total, d_cnt};
   CandList rl{redo, (unsigned long long)ne_total, d_cnt + 2};
-  CK(launch_k(true, k_classify, dim3((unsigned)((ne_total + TB - 1) / TB)), dim3(TB), 0, st, d_inst, eoff, n, ne_total,
-              cl, d_cnt));
-  if (prof) CK(record(s.ev[3], st, capturing));
+  {
+    // a1-a4 in one cooperative launch (every block resident for its grid
+    // barriers); its barrier counters are in d_cnt[22], zeroed above
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prep, TB, 0));
+    occ = std::max(1, std::min(occ, 4));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(c->n_sm * occ));
+    lc.blockDim = dim3(TB);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&lc, k_prep, d_inst, (const long long*)d_off, n, nf_total, ne_total, cl, d_cnt,
+                          reinterpret_cast<unsigned*>(d_cnt + 22)));
+  }
+  if (prof) {
+    // the three phases are one kernel: their times are reported together
+    CK(record(s.ev[1], st, capturing));
+    CK(record(s.ev[2], st, capturing));
+    CK(record(s.ev[3], st, capturing));
+  }
   const ExLayout Lf = ex_layout(pmax, qmax, 4), Ld = ex_layout(pmax, qmax, 8);
   const int WPB = TB / 32;
   if ((long long)Ld.total * WPB > c->smem_optin)
@@ -783,6 +797,7 @@ dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t
     cudaEventElapsedTime(&S.ms_redo, s.ev[5], s.ev[4]);
     cudaEventElapsedTime(&S.ms_total, s.ev[0], s.ev[4]);
   }
+  if ((s.h_cnt[22] >> 32) != 0) return fail(DC_EINTERNAL, "a grid barrier of the hole-map kernel timed out");
   if (err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
   if (err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");
   if (err & (ERR_ROUNDS | ERR_RECHECK))
@@ -1260,11 +1275,13 @@ dc_status dc_poll(dc_ctx* c, uint64_t ticket, int64_t timeout_us) {
         CK(cudaStreamSynchronize(s->stream));
         int err = 0;
         for (int i = 0; i < s->n_inst; ++i) err |= s->h_inst[i].err;
+        const bool barrier_out = (s->h_cnt[22] >> 32) != 0;
         if (s->host_out) {
           memcpy(s->user_flags, s->h_flags, (size_t)s->out_n);
           if (s->user_dist) memcpy(s->user_dist, s->h_dist, sizeof(double) * s->out_n);
         }
         s->busy = false;
+        if (barrier_out) return fail(DC_EINTERNAL, "a grid barrier of the hole-map kernel timed out");
         if (err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
         if (err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");
         if (err & (ERR_ROUNDS | ERR_RECHECK)) return fail(DC_EINTERNAL, "exact test capacity exceeded (0x%x)", err);

@@ -5,8 +5,8 @@
 //
 // The node array is the one place the whole grid is read ((p+1)^3 x 3 FP64 per
 // element, 170 MB at 64^3 Q2), so it is read as contiguous tiles: a block
-// takes `eb` consecutive elements at a time (eb * (p+1)^3 * 24 bytes, at most
-// 48 KB), one thread copies each tile into shared memory with a bulk
+// takes `eb` consecutive elements at a time (eb * (p+1)^3 * 24 bytes, about
+// 16 KB), one thread copies each tile into shared memory with a bulk
 // asynchronous copy (cp.async.bulk, completion counted on an mbarrier) while
 // the block works on the previous tile (two buffers), and the block writes its
 // boxes, origins and frame coordinates from shared memory in element order,
@@ -26,13 +26,17 @@
 namespace dc {
 
 constexpr int FR_THREADS = 256;
-constexpr int FR_MAX_TILE_BYTES = 48 * 1024;
+// tiles of about 16 KB: with two buffers a block holds 32 KB, so up to eight
+// blocks share an SM and keep as many tiles in flight
+constexpr int FR_MAX_TILE_BYTES = 16 * 1024;
 constexpr unsigned FR_WAIT_LIMIT = 1u << 22;  // try_wait polls before a wait gives up
 
-// elements per tile: the largest power of two (<= 128) whose nodes fit 48 KB
+// elements per tile: the largest power of two (<= 128) whose nodes fit the
+// tile, but at least 8 (a group of FR_THREADS / eb <= 32 threads reduces one
+// element's nodes within a warp)
 __host__ __device__ inline int frames_tile_elems(int npe) {
   int eb = 128;
-  while (eb > 1 && (long long)eb * npe * 24 > FR_MAX_TILE_BYTES) eb >>= 1;
+  while (eb > 8 && (long long)eb * npe * 24 > FR_MAX_TILE_BYTES) eb >>= 1;
   return eb;
 }
 

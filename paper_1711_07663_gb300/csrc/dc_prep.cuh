@@ -74,16 +74,16 @@ __device__ void grid_from_box(Inst& in) {
 // SURF_FPB faces, instances): threads transform nodes, then one thread per
 // (face, axis) takes the face's box from shared memory; the last block of an
 // instance to finish derives its hole-map grid.
-__global__ void __launch_bounds__(256) k_surface(Inst* __restrict__ I) {
-  pdl_enter();
+// SURF_FPB faces of instance `in` from face f0 (one block): pose, face boxes,
+// and the block's share of the surface box and face extents.  With
+// derive_grid, the last block of the instance to finish derives its hole-map
+// grid (the fused prep kernel derives it after a grid barrier instead).
+__device__ void surface_tile(Inst& in, long long f0, bool derive_grid) {
   __shared__ double s_x[SURF_FPB * MAX_NPF * 3];
   __shared__ unsigned long long s_key[6];
   __shared__ unsigned s_ext[3];
   __shared__ int s_last;
-  Inst& in = I[blockIdx.y];
   const long long F = in.n_faces;
-  const long long f0 = (long long)blockIdx.x * SURF_FPB;
-  if (f0 >= F) return;
   const int nf = (int)min((long long)SURF_FPB, F - f0);
   const int npf = (in.q + 1) * (in.q + 1);
   const int nval = nf * npf * 3;
@@ -135,34 +135,53 @@ __global__ void __launch_bounds__(256) k_surface(Inst* __restrict__ I) {
     atomicMax(&in.sbox_key[3 + threadIdx.x], s_key[3 + threadIdx.x]);
     atomicMax(&in.fext_bits[threadIdx.x], s_ext[threadIdx.x]);
   }
-  // the last block of this instance derives the grid
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned nblk = (unsigned)((F + SURF_FPB - 1) / SURF_FPB);
-    s_last = atomicAdd(&in.surf_done, 1u) == nblk - 1;
-  }
-  __syncthreads();
-  if (s_last && threadIdx.x == 0) {
+  if (derive_grid) {
+    // the last block of this instance derives the grid
     __threadfence();
-    grid_from_box(in);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned nblk = (unsigned)((F + SURF_FPB - 1) / SURF_FPB);
+      s_last = atomicAdd(&in.surf_done, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      __threadfence();
+      grid_from_box(in);
+    }
   }
+  __syncthreads();  // the shared arrays may be reused by the next tile
 }
 
-__global__ void k_clear(Inst* __restrict__ I) {
+// Pose transform (rounded exactly as ((R0 x + R1 y) + R2 z) + t, no fusion),
+// per-face node boxes, surface box and largest face extent.  Grid (blocks of
+// SURF_FPB faces, instances): threads transform nodes, then one thread per
+// (face, axis) takes the face's box from shared memory; the last block of an
+// instance to finish derives its hole-map grid.
+__global__ void __launch_bounds__(256) k_surface(Inst* __restrict__ I) {
   pdl_enter();
   Inst& in = I[blockIdx.y];
+  const long long f0 = (long long)blockIdx.x * SURF_FPB;
+  if (f0 >= in.n_faces) return;
+  surface_tile(in, f0, true);
+}
+
+// zero the hole map, the bin counts and the row counters of one instance;
+// thread `t` of `nt` takes every nt-th word
+__device__ void clear_inst(Inst& in, long long t, long long nt) {
   long long ncube = (long long)in.dims[1] * in.dims[2] * CUBE_PITCH;
   int nb = in.bdims[0] * in.bdims[1] * in.bdims[2];
   if (nb > in.nbins_cap) nb = 0;
   uint4* c4 = reinterpret_cast<uint4*>(in.cube);
   long long n4 = ncube / 16;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (long long)gridDim.x * blockDim.x)
-    c4[k] = make_uint4(0, 0, 0, 0);
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += (long long)gridDim.x * blockDim.x)
-    in.bin_cnt[k] = 0;
+  for (long long k = t; k < n4; k += nt) c4[k] = make_uint4(0, 0, 0, 0);
+  for (long long k = t; k < nb; k += nt) in.bin_cnt[k] = 0;
   const int nrows = in.dims[1] * in.dims[2];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nrows; k += gridDim.x * blockDim.x) in.row_cnt[k] = 0;
+  for (long long k = t; k < nrows; k += nt) in.row_cnt[k] = 0;
+}
+
+__global__ void k_clear(Inst* __restrict__ I) {
+  pdl_enter();
+  clear_inst(I[blockIdx.y], (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 __device__ __forceinline__ int cube_floor(double x, int n) {
@@ -180,9 +199,8 @@ __device__ __forceinline__ int cube_floorf(float x, int n) {
 }
 
 // a3: NEAR tags of the hole map, and face -> bin (bin of the box's min corner)
-__global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total) {
-  pdl_enter();
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void tag_face(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total,
+                         long long g) {
   if (g >= nf_total) return;
   int ii = find_inst(foff, n_inst, g);
   Inst& in = I[ii];
@@ -211,15 +229,18 @@ __global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, 
   atomicAdd(&in.bin_cnt[bi], 1);
 }
 
+__global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total) {
+  pdl_enter();
+  tag_face(I, foff, n_inst, nf_total, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // exclusive scan of the bin counts (one CTA of 1024 threads per instance):
 // thread t takes the t-th chunk of consecutive bins (held in registers when a
 // chunk has at most BIN_PER_T bins, else read twice), the CTA scans the chunk
 // totals with warp shuffles; counts become cursors
 constexpr int BIN_PER_T = 10;
-__global__ void __launch_bounds__(1024) k_bin_scan(Inst* __restrict__ I) {
-  pdl_enter();
+__device__ void bin_scan_inst(Inst& in) {
   __shared__ int wsum[32];
-  Inst& in = I[blockIdx.x];
   const int nb = in.bdims[0] * in.bdims[1] * in.bdims[2];
   if ((in.err & ERR_DEGENERATE) || nb > in.nbins_cap) return;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5, T = blockDim.x;
@@ -274,6 +295,12 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Inst* __restrict__ I) {
     }
   }
   if (t == T - 1) in.bin_off[nb] = wsum[(T >> 5) - 1];
+  __syncthreads();  // wsum may be reused by the next instance
+}
+
+__global__ void __launch_bounds__(1024) k_bin_scan(Inst* __restrict__ I) {
+  pdl_enter();
+  bin_scan_inst(I[blockIdx.x]);
 }
 
 __device__ __forceinline__ void bin_fill(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst,
@@ -452,12 +479,8 @@ __global__ void __launch_bounds__(256) k_fill_cross(Inst* __restrict__ I, const 
 }
 
 // one warp per row: winding number of each cube that is not NEAR
-__global__ void __launch_bounds__(256) k_row_label(Inst* __restrict__ I) {
-  pdl_enter();
-  Inst& in = I[blockIdx.y];
+__device__ void row_label(Inst& in, int r, int lane) {
   if (in.err & (ERR_DEGENERATE | ERR_NONFINITE)) return;
-  const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nrows = in.dims[1] * in.dims[2];
   if (r >= nrows) return;
   const int cnt = in.row_cnt[r];
@@ -484,6 +507,11 @@ __global__ void __launch_bounds__(256) k_row_label(Inst* __restrict__ I) {
     v = (v & ~(0xffu << (8 * k))) | (st << (8 * k));
   }
   *word = v;
+}
+
+__global__ void __launch_bounds__(256) k_row_label(Inst* __restrict__ I) {
+  pdl_enter();
+  row_label(I[blockIdx.y], blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------ a4: classify + compact
@@ -514,12 +542,12 @@ __device__ __forceinline__ int point_label(const Inst& in, float x, float y, flo
 }
 
 
-__global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const long long* __restrict__ eoff, int n_inst,
-                                                  long long ne_total, CandList cl,
-                                                  unsigned long long* __restrict__ cnt) {
-  pdl_enter();
+// element g (every lane of a warp calls it; g past the end is a no-op lane):
+// box against the hole map -> hole / field written, or listed as a candidate
+__device__ void classify_elem(Inst* __restrict__ I, const long long* __restrict__ eoff, int n_inst,
+                              long long ne_total, const CandList& cl, unsigned long long* __restrict__ cnt,
+                              long long g) {
   const unsigned FULL = 0xffffffffu;
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = g < ne_total;
   bool cand = false, hole = false;
   int ii = 0;
@@ -592,6 +620,104 @@ __global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const lo
       if (pos < cl.cap) cl.cand[pos] = ((unsigned long long)ii << 40) | (unsigned long long)e;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_classify(Inst* __restrict__ I, const long long* __restrict__ eoff, int n_inst,
+                                                  long long ne_total, CandList cl,
+                                                  unsigned long long* __restrict__ cnt) {
+  pdl_enter();
+  classify_elem(I, eoff, n_inst, ne_total, cl, cnt, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ------------------------------------------------------------------ the fused prep
+// Grid barrier of the fused prep kernel.  The kernel is launched cooperatively,
+// so every block is resident: each block's first thread makes the block's
+// writes visible (fence), arrives, and waits with acquire loads until every
+// block of the grid has arrived at this barrier (the count is never reset
+// within a launch: barrier k waits for k * gridDim.x arrivals).  The wait is
+// bounded: a wait that runs out sets *timed_out, which every later barrier
+// sees, and the kernel leaves.
+constexpr unsigned PREP_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool prep_barrier(unsigned* count, unsigned k, unsigned* timed_out) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = ld_acquire_gpu(timed_out) == 0u;
+    if (ok) {
+      __threadfence();
+      atomicAdd(count, 1u);
+      const unsigned target = k * gridDim.x;
+      for (unsigned it = 0; ld_acquire_gpu(count) < target; ++it) {
+        if (it >= PREP_WAIT_LIMIT || ld_acquire_gpu(timed_out) != 0u) {
+          atomicExch(timed_out, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The surface ingest, hole map, face bins and element classification of a
+// cut (a1-a4) in one cooperative launch: the seven steps are each a
+// grid-stride loop over their work, separated by grid barriers, which leaves
+// the launch and drain of seven small kernels out of the chain.  sync[0]
+// counts barrier arrivals, sync[1] records a barrier that ran out (the cut
+// then reports an internal error).
+__global__ void __launch_bounds__(256) k_prep(Inst* __restrict__ I, const long long* __restrict__ off, int n_inst,
+                                              long long nf_total, long long ne_total, CandList cl,
+                                              unsigned long long* __restrict__ cnt, unsigned* __restrict__ sync) {
+  pdl_enter();
+  const long long* foff = off;
+  const long long* eoff = off + n_inst + 1;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = tid >> 5, nwarp = nthr >> 5;
+  unsigned k = 0;
+  // a1 + a2: pose and face boxes, SURF_FPB faces per block and step
+  for (int ii = 0; ii < n_inst; ++ii) {
+    Inst& in = I[ii];
+    const long long nt = (in.n_faces + SURF_FPB - 1) / SURF_FPB;
+    for (long long t = blockIdx.x; t < nt; t += gridDim.x) surface_tile(in, t * SURF_FPB, false);
+  }
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  for (long long ii = tid; ii < n_inst; ii += nthr) grid_from_box(I[ii]);
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  // a3: clear the map and counters, then tag NEAR cubes and count bins
+  for (int ii = 0; ii < n_inst; ++ii) clear_inst(I[ii], tid, nthr);
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  for (long long g = tid; g < nf_total; g += nthr) tag_face(I, foff, n_inst, nf_total, g);
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  for (int ii = blockIdx.x; ii < n_inst; ii += gridDim.x) bin_scan_inst(I[ii]);
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  // faces into their bins, and the row centre lines' crossings
+  for (long long g = tid; g < nf_total; g += nthr) bin_fill(I, foff, n_inst, nf_total, g);
+  for (int ii = 0; ii < n_inst; ++ii) {
+    Inst& in = I[ii];
+    const long long ntri = in.n_faces * 2LL * in.q * in.q;
+    for (long long g = tid; g < ntri; g += nthr) row_cross(in, g);
+  }
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  for (int ii = 0; ii < n_inst; ++ii) {
+    Inst& in = I[ii];
+    const long long nrows = (long long)in.dims[1] * in.dims[2];
+    for (long long r = gwarp; r < nrows; r += nwarp) row_label(in, (int)r, lane);
+  }
+  if (!prep_barrier(sync, ++k, sync + 1)) return;
+  // a4: every element against the map (warps step together for the compaction)
+  for (long long base = tid - lane; base < ne_total; base += nthr) classify_elem(I, eoff, n_inst, ne_total, cl, cnt, base + lane);
 }
 
 }  // namespace dc

@@ -110,12 +110,14 @@ typedef struct {
     int32_t max_inflight;     /* serving slots for dc_submit, 1..64; 0 -> 4 */
     int32_t profile;          /* 1: time each phase with CUDA events (dc_get_stats) */
     int32_t reserve_faces;    /* dc_create sizes every slot's device arena and pinned
-                                 staging for one request of this many order-4 faces on
-                                 the largest mesh, so requests up to that size never
-                                 allocate (larger ones grow the slot first); 0 -> 8192,
-                                 -1 -> reserve nothing (grow on first use).  A
-                                 reservation that would exceed mem_budget_bytes is
-                                 skipped. */
+                                 staging (instance records, counters, host flags, host
+                                 face nodes of dc_submit) for one request of this many
+                                 order-2 faces on the largest mesh, from one device block
+                                 and one pinned block, so such requests never allocate
+                                 (larger ones, and the first dc_submit with host
+                                 distances, grow the slot first); 0 -> 8192, -1 ->
+                                 reserve nothing (grow on first use).  A reservation
+                                 that would exceed mem_budget_bytes is skipped. */
 } dc_config;
 
 typedef struct {
@@ -150,9 +152,10 @@ typedef struct {
     int64_t fallbacks;        /* elements redone in FP64 after a list overflow */
     int64_t holemap_rows_undecided; /* hole-map rows whose surface crossings could not be
                                        certified (their cubes are left "near") */
-    float ms_surface;         /* profile=1 only: pose + face boxes + hole map tags + bins */
-    float ms_holemap;         /* connected components + winding-number seeds */
-    float ms_classify;        /* hole-map lookup + candidate compaction */
+    float ms_surface;         /* profile=1 only: pose, face boxes, hole map, bins and the
+                                 element classification (one fused kernel) */
+    float ms_holemap;         /* 0: part of ms_surface (kept for the layout) */
+    float ms_classify;        /* 0: part of ms_surface (kept for the layout) */
     float ms_exact;           /* exact element-face tests + sign (main pass) */
     float ms_redo;            /* FP64 pass over elements whose FP32 re-solve list overflowed */
     float ms_total;
@@ -273,7 +276,7 @@ const char *dc_last_error(const dc_ctx *ctx);
  * process exits; the call makes no cudaMalloc/cudaFree (nor any other
  * allocating call).  Sizes whose scratch does not fit are rejected with
  * DC_EINVAL and a message giving the bytes needed (40 bytes per element, about
- * 250 bytes per Q2 face or 630 per Q4 face, plus 2.6 MiB: 65,536 elements with
+ * 270 bytes per Q2 face or 660 per Q4 face, plus 2.6 MiB: 65,536 elements with
  * 8,192 Q2 faces fit).  The hole map uses 64 cubes on the longest side and 4-cube
  * face bins, the bulk tests FP32 with FP64 re-solve (flags identical to
  * dc_cut).

@@ -183,6 +183,7 @@ struct Slot {
   int8_t* h_flags = nullptr;     // pinned output staging (serving, host outputs)
   double* h_dist = nullptr;
   size_t h_out_cap = 0;
+  size_t h_dist_cap = 0;
   // pinned copy of a submitted request's host face nodes: dc_submit copies
   // them here before it returns, and the upload reads this copy, so the caller
   // may reuse its buffer at once (a slot is reused only after its ticket is
@@ -203,6 +204,12 @@ struct Slot {
   bool near = false;       // the flags-only split ran
   int cur_ring = 0;
 };
+
+// face order the slots' reservation at dc_create is sized for
+constexpr int RESERVE_Q = 2;
+// prefix offsets over a batch's instances, each n + 1 long: faces, elements,
+// k_prep's surface tiles, surface triangles
+constexpr int NOFF = 4;
 
 constexpr int NCNT = 24;  // [0,1] candidates/cursor, [2,3] redo/cursor, [4..10] exact counters,
                           // [22] the prep kernel's barrier count (low half) and time-out flag,
@@ -327,14 +334,14 @@ struct SurfNeed {
 
 // bytes of arena a batch of surfaces over ne_total elements needs
 size_t arena_bytes(const dc_ctx* c, const std::vector<SurfNeed>& v, long long ne_total) {
-  size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * 2 * (v.size() + 1));
+  size_t s = al256(sizeof(Inst) * v.size()) + al256(sizeof(long long) * NOFF * (v.size() + 1));
   int nb = nbins_cap(bin_floor(c->cfg));
   for (auto& r : v) {
     long long F = r.F;
     int npf = (r.q + 1) * (r.q + 1);
     if (r.staged) s += al256(sizeof(double) * F * npf * 3);  // staged input faces
     if (c->cfg.precision == DC_HEURISTIC) s += al256(sizeof(float) * 16 * F);
-    s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(float) * F * 6) +
+    s += al256(sizeof(double) * F * npf * 3) + al256(sizeof(float) * F * 6) * 2 +
          al256(sizeof(int) * F) * 2 + al256(cube_bytes()) + al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) +
          run_bytes();
   }
@@ -394,7 +401,10 @@ dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
   return DC_OK;
 }
 
-dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total) {
+// host staging of a slot: the instance ring, counters, the flags of host
+// outputs, and (want_host_dist: a submitted request with host distances) their
+// distances
+dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total, bool want_host_dist) {
   if (s.h_inst_cap < n_inst) {
     for (int r = 0; r < Slot::RING; ++r) {
       if (s.ring_used[r]) CK(cudaEventSynchronize(s.ring_ev[r]));
@@ -406,7 +416,7 @@ dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total) {
     }
     for (int r = 0; r < Slot::RING; ++r) {
       CK(cudaMallocHost(&s.ring_inst[r], sizeof(Inst) * n_inst));
-      CK(cudaMallocHost(&s.ring_off[r], sizeof(long long) * 2 * (n_inst + 1)));
+      CK(cudaMallocHost(&s.ring_off[r], sizeof(long long) * NOFF * (n_inst + 1)));
     }
     s.h_inst_cap = n_inst;
   }
@@ -422,12 +432,15 @@ dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total) {
   if (!s.h_cnt) CK(cudaMallocHost(&s.h_cnt, sizeof(unsigned long long) * NCNT));
   if ((long long)s.h_out_cap < ne_total) {
     host_free(c, s.h_flags);
-    host_free(c, s.h_dist);
     s.h_flags = nullptr;
-    s.h_dist = nullptr;
     CK(cudaMallocHost(&s.h_flags, (size_t)ne_total));
-    CK(cudaMallocHost(&s.h_dist, sizeof(double) * ne_total));
     s.h_out_cap = (size_t)ne_total;
+  }
+  if (want_host_dist && (long long)s.h_dist_cap < ne_total) {
+    host_free(c, s.h_dist);
+    s.h_dist = nullptr;
+    CK(cudaMallocHost(&s.h_dist, sizeof(double) * ne_total));
+    s.h_dist_cap = (size_t)ne_total;
   }
   return DC_OK;
 }
@@ -627,7 +640,10 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   }
   dc_status rc = ensure_arena(c, s, arena_need(c, v, ne_total));
   if (rc) return rc;
-  rc = ensure_host(c, s, (size_t)n, ne_total);
+  bool host_dist = false;
+  if (copy_inputs)
+    for (auto& r : v) host_dist |= !r.req->on_device && r.req->dist_out != nullptr;
+  rc = ensure_host(c, s, (size_t)n, ne_total, host_dist);
   if (rc) return rc;
   size_t host_face_doubles = 0;
   if (copy_inputs) {
@@ -641,9 +657,9 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   char* p = s.arena.base;
   auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return r; };
   Inst* d_inst = (Inst*)take(sizeof(Inst) * n);
-  long long* d_off = (long long*)take(sizeof(long long) * 2 * (n + 1));
+  long long* d_off = (long long*)take(sizeof(long long) * NOFF * (n + 1));
   const int nb = nbins_cap(bin_floor(c->cfg));
-  long long fo = 0, eo = 0;
+  long long fo = 0, eo = 0, to = 0, tro = 0;
   for (int i = 0; i < n; ++i) {
     const dc_request* r = v[i].req;
     const Mesh& m = c->meshes[v[i].mesh];
@@ -678,6 +694,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     in.fbox = (float*)take(sizeof(float) * F * 6);
     in.fbin = (int*)take(sizeof(int) * F);
     in.bin_faces = (int*)take(sizeof(int) * F);
+    in.bin_fbox = (float*)take(sizeof(float) * F * 6);
     in.cube = (uint8_t*)take(cube_bytes());
     in.bin_cnt = (int*)take(sizeof(int) * nb);
     in.bin_off = (int*)take(sizeof(int) * (nb + 1));
@@ -697,11 +714,17 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     for (int a = 0; a < 3; ++a) { in.sbox_key[a] = ~0ULL; in.sbox_key[3 + a] = 0ULL; }
     s.h_off[i] = fo;
     s.h_off[n + 1 + i] = eo;
+    s.h_off[2 * (n + 1) + i] = to;
+    s.h_off[3 * (n + 1) + i] = tro;
     fo += F;
     eo += m.n_elem;
+    to += (F + SURF_FPB - 1) / SURF_FPB;
+    tro += F * 2LL * r->q * r->q;
   }
   s.h_off[n] = fo;
   s.h_off[2 * n + 1] = eo;
+  s.h_off[3 * n + 2] = to;
+  s.h_off[4 * n + 3] = tro;
   unsigned long long* cand = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* redo = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
   unsigned long long* fulll = (unsigned long long*)take(sizeof(unsigned long long) * ne_total);
@@ -728,7 +751,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   }
 
   CK(cudaMemcpyAsync(d_inst, s.h_inst, sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_off, s.h_off, sizeof(long long) * 2 * (n + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_off, s.h_off, sizeof(long long) * NOFF * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(s.ring_ev[s.cur_ring], st));
   s.ring_used[s.cur_ring] = true;
   LaunchParams lp;
@@ -956,7 +979,7 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     dc_status st = init_slot(s, cfg.profile);
     if (st) return bail(st);
   }
-  int* d_bad = nullptr;  // [0]: a node is not finite; [1]: a node copy failed; bytes 8..15: sum of extents
+  int* d_bad = nullptr;  // [0]: a node is not finite; bytes 8..15: sum of element extents
   if (cudaMalloc(&d_bad, 16) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
   double* d_ext = reinterpret_cast<double*>(reinterpret_cast<char*>(d_bad) + 8);
   cudaStream_t st = c->slots[0].stream;
@@ -985,7 +1008,9 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
       return bail(fail(DC_ECUDA, "mesh %d: copying nodes failed", i));
     }
     cudaMemsetAsync(d_bad, 0, 16, st);
-    const cudaError_t fe = launch_frames(m.nodes, md.n_elem, (int)npe, m.box, nullptr, nullptr, d_bad, d_ext, c->n_sm, st);
+    k_elem_boxes<<<(unsigned)std::min<long long>((md.n_elem + 63) / 64, (long long)c->n_sm * 8), 256, 0, st>>>(
+        m.nodes, md.n_elem, (int)npe, m.box, d_bad, d_ext);
+    const cudaError_t fe = cudaGetLastError();
     int bad[2] = {0, 0};
     double ext = 0.0;
     if (fe != cudaSuccess || cudaMemcpyAsync(bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -995,10 +1020,6 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
       cudaFree(d_bad);
       return bail(fail(DC_ECUDA, "mesh %d: element boxes failed: %s", i,
                        cudaGetErrorString(fe != cudaSuccess ? fe : cudaGetLastError())));
-    }
-    if (bad[1]) {
-      cudaFree(d_bad);
-      return bail(fail(DC_EINTERNAL, "mesh %d: a bulk copy of element nodes did not complete", i));
     }
     if (bad[0]) {
       cudaFree(d_bad);
@@ -1012,17 +1033,17 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     // dc_cut and dc_submit of such requests allocate nothing while serving
     long long ne_max = 0;
     for (auto& m : c->meshes) ne_max = std::max(ne_max, m.n_elem);
-    const std::vector<SurfNeed> one{{(long long)cfg.reserve_faces, MAX_Q, true}};
+    const std::vector<SurfNeed> one{{(long long)cfg.reserve_faces, RESERVE_Q, true}};
     const size_t need = al256(arena_bytes(c, one, ne_max));
-    const size_t stage = (size_t)cfg.reserve_faces * (MAX_Q + 1) * (MAX_Q + 1) * 3;
+    const size_t stage = (size_t)cfg.reserve_faces * (RESERVE_Q + 1) * (RESERVE_Q + 1) * 3;
     const size_t n_slots = c->slots.size();
     auto serving = [&](size_t i) { return i > 0 || n_slots == 1; };
     // host staging of one slot: instance ring, counters, outputs, and the
     // face copy of a submitted request (serving slots)
-    const size_t ring_one = al256(sizeof(Inst)) + al256(sizeof(long long) * 4);
+    const size_t ring_one = al256(sizeof(Inst)) + al256(sizeof(long long) * NOFF * 2);
     auto host_need = [&](size_t i) {
       return Slot::RING * ring_one + al256(sizeof(unsigned long long) * NCNT) + al256((size_t)ne_max) +
-             al256(sizeof(double) * ne_max) + (serving(i) ? al256(sizeof(double) * stage) : 0);
+             (serving(i) ? al256(sizeof(double) * stage) : 0);
     };
     size_t host_total = 0;
     for (size_t i = 0; i < n_slots; ++i) host_total += host_need(i);
@@ -1046,12 +1067,11 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
         c->arena_bytes += need;
         for (int r = 0; r < Slot::RING; ++r) {
           s.ring_inst[r] = reinterpret_cast<Inst*>(take(sizeof(Inst)));
-          s.ring_off[r] = reinterpret_cast<long long*>(take(sizeof(long long) * 4));
+          s.ring_off[r] = reinterpret_cast<long long*>(take(sizeof(long long) * NOFF * 2));
         }
         s.h_inst_cap = 1;
         s.h_cnt = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * NCNT));
         s.h_flags = reinterpret_cast<int8_t*>(take((size_t)ne_max));
-        s.h_dist = reinterpret_cast<double*>(take(sizeof(double) * ne_max));
         s.h_out_cap = (size_t)ne_max;
         if (serving(i)) {
           s.h_faces = reinterpret_cast<double*>(take(sizeof(double) * stage));
@@ -1383,7 +1403,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   size_t need = al256(sizeof(Inst)) + al256(sizeof(long long) * 4) + al256(sizeof(float) * 6 * n_elem) +
                 al256(sizeof(unsigned long long) * n_elem) * 2 + al256(sizeof(unsigned long long) * NCNT) +
                 al256(sizeof(double) * n_faces * npf * 3) +
-                al256(sizeof(float) * n_faces * 6) + al256(sizeof(int) * n_faces) * 2 + al256(cube_bytes()) +
+                al256(sizeof(float) * n_faces * 6) * 2 + al256(sizeof(int) * n_faces) * 2 + al256(cube_bytes()) +
                 al256(sizeof(int) * nb) + al256(sizeof(int) * (nb + 1)) + run_bytes() + al256(sizeof(int));
   if (need > NOALLOC_SCRATCH_BYTES)
     return fail(DC_EINVAL, "dc_cut_noalloc: %lld elements (p=%d) and %lld faces (q=%d) need %zu bytes of scratch; "
@@ -1403,11 +1423,9 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   const int WPB = TB / 32;
   if ((long long)Ld.total * WPB > D.smem_optin)
     return fail(DC_EINVAL, "orders p=%d q=%d need %d bytes of shared memory per block", p, q, Ld.total * WPB);
-  int occ = 0, occd = 0, occf = 0;
+  int occ = 0, occd = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occd, k_exact<double>, TB, (size_t)Ld.total * WPB));
-  CK(cudaFuncSetAttribute(k_elem_frames, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frames_smem(npe)));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, k_elem_frames, FR_THREADS, frames_smem(npe)));
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* pp = D.scratch;
   auto take = [&](size_t bytes) { unsigned char* r = pp; pp += al256(bytes); return r; };
@@ -1434,6 +1452,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   h.fbox = (float*)take(sizeof(float) * n_faces * 6);
   h.fbin = (int*)take(sizeof(int) * n_faces);
   h.bin_faces = (int*)take(sizeof(int) * n_faces);
+  h.bin_fbox = (float*)take(sizeof(float) * n_faces * 6);
   h.cube = (uint8_t*)take(cube_bytes());
   h.bin_cnt = (int*)take(sizeof(int) * nb);
   h.bin_off = (int*)take(sizeof(int) * (nb + 1));
@@ -1442,7 +1461,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
     h.row_cnt = (int*)take(sizeof(int) * rows);
     h.row_x = (int*)take(sizeof(int) * rows * ROW_XCAP);
   }
-  int* d_bad = (int*)take(sizeof(int) * 2);  // [0] non-finite node, [1] a node copy failed
+  int* d_bad = (int*)take(sizeof(int) * 2);  // [0] a non-finite node
   h.nbins_cap = nb;
   h.tol = tol;
   h.tol_f = float_up(tol);
@@ -1470,12 +1489,8 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CKQ(cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
   CKQ(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
   CKQ(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
-  {
-    const int eb = frames_tile_elems(npe);
-    const long long grid = std::min<long long>((n_elem + eb - 1) / eb, (long long)D.n_sm * std::max(occf, 1));
-    k_elem_frames<<<(unsigned)grid, FR_THREADS, frames_smem(npe), st>>>(nodes, n_elem, npe, eb, ebox, nullptr,
-                                                                        nullptr, d_bad, nullptr, d_bad + 1);
-  }
+  k_elem_boxes<<<(unsigned)std::min<long long>((n_elem + 63) / 64, (long long)D.n_sm * 8), 256, 0, st>>>(
+      nodes, n_elem, npe, ebox, d_bad, nullptr);
   unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
   k_surface<<<dim3((unsigned)((n_faces + SURF_FPB - 1) / SURF_FPB), 1), TB, 0, st>>>(d_inst);
   k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);
@@ -1494,7 +1509,6 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CKQ(cudaMemcpyAsync(bad, d_bad, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
   CKQ(cudaStreamSynchronize(st));
 #undef CKQ
-  if (bad[1]) return fail(DC_EINTERNAL, "a bulk copy of element nodes did not complete");
   if (bad[0]) return fail(DC_EINVAL, "an element node is NaN or infinite");
   if (h.err & ERR_NONFINITE) return fail(DC_EINVAL, "a face node is NaN or infinite");
   if (h.err & ERR_DEGENERATE) return fail(DC_EINVAL, "the cut surface has zero extent");

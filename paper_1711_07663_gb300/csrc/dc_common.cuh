@@ -64,6 +64,7 @@ struct Inst {
   int* bin_cnt;            // [nbins]
   int* bin_off;            // [nbins + 1]
   int* bin_faces;          // [n_faces]
+  float* bin_fbox;         // [n_faces][6] the face boxes in bin order (beside bin_faces)
   int nbins_cap;
   int* row_cnt;            // surface crossings per hole-map row [rows] (+ROW_UNDECIDED: undecided)
   int* row_x;              // crossings (cube x << 1 | entering) [rows][ROW_XCAP]

@@ -689,7 +689,7 @@ __device__ void gather_round(WarpCtx<T>& W, WarpState<T>& S, double r, const flo
           float lb = 0.f, key = 0.f;
           if (k < f1) {
             f = in.bin_faces[k];
-            const float* fb = in.fbox + 6 * (long long)f;
+            const float* fb = in.bin_fbox + 6 * (long long)k;  // the box beside the id
             float b[6] = {fb[0], fb[1], fb[2], fb[3], fb[4], fb[5]};
             float fm = 0.f;
             for (int a = 0; a < 6; ++a) fm = fmaxf(fm, fabsf(b[a]));

@@ -1,14 +1,16 @@
-// dc_frames.cuh -- the sweep over every element node (the cold path of a
-// resident grid): element node boxes rounded outward and, when asked, the
-// element frame every exact test uses (origin at the centre of the float box,
-// node coordinates relative to it rounded to float, [e][x|y|z block][node]).
+// dc_frames.cuh -- the sweeps over every element node (the cold path of a
+// grid): element node boxes rounded outward (k_elem_boxes, every resident
+// grid and the allocation-free cut) and, for the donor search's grid, also the
+// element frame (k_elem_frames: origin at the centre of the float box, node
+// coordinates relative to it rounded to float, [e][x|y|z block][node]).
 //
 // The node array is the one place the whole grid is read ((p+1)^3 x 3 FP64 per
 // element, 170 MB at 64^3 Q2), so it is read as contiguous tiles: a block
-// takes `eb` consecutive elements at a time (eb * (p+1)^3 * 24 bytes, about
-// 16 KB), one thread copies each tile into shared memory with a bulk
-// asynchronous copy (cp.async.bulk, completion counted on an mbarrier) while
-// the block works on the previous tile (two buffers), and the block writes its
+// takes `eb` consecutive elements at a time (eb * (p+1)^3 * 24 bytes, at most
+// 48 KB), one thread copies each tile into shared memory with a bulk
+// asynchronous copy (cp.async.bulk, completion counted on an mbarrier) ahead
+// of its use (two buffers: the next copy is in flight while the block works on
+// the current tile), and the block writes its
 // boxes, origins and frame coordinates from shared memory in element order,
 // so every global access of the sweep is a contiguous span.  Tiles whose
 // global address or size is not a multiple of 16 bytes (a node array that is
@@ -26,9 +28,10 @@
 namespace dc {
 
 constexpr int FR_THREADS = 256;
-// tiles of about 16 KB: with two buffers a block holds 32 KB, so up to eight
-// blocks share an SM and keep as many tiles in flight
-constexpr int FR_MAX_TILE_BYTES = 16 * 1024;
+// a ring of FR_STAGES tile buffers of at most 48 KB: a block keeps
+// FR_STAGES - 1 copies in flight while it reduces the tile it holds
+constexpr int FR_STAGES = 2;
+constexpr int FR_MAX_TILE_BYTES = 48 * 1024;
 constexpr unsigned FR_WAIT_LIMIT = 1u << 22;  // try_wait polls before a wait gives up
 
 // elements per tile: the largest power of two (<= 128) whose nodes fit the
@@ -84,7 +87,7 @@ __device__ __forceinline__ bool fr_bar_wait(uint64_t* bar, unsigned parity) {
 }
 
 // grid: persistent blocks of FR_THREADS threads, dynamic shared memory
-// 2 * eb * npe * 24 bytes (two tile buffers).  loc/org may be null (boxes
+// FR_STAGES * eb * npe * 24 bytes (the tile buffers).  loc/org may be null (boxes
 // only), ext_sum may be null.
 __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __restrict__ nodes, long long n_elem,
                                                             int npe, int eb, float* __restrict__ box,
@@ -92,14 +95,13 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
                                                             int* __restrict__ bad, double* __restrict__ ext_sum,
                                                             int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[FR_STAGES];
   __shared__ double s_org[128][3];
   __shared__ double s_ext[FR_THREADS / 32];
   __shared__ int s_bad;
   const int tid = threadIdx.x;
   const long long tile_doubles = (long long)eb * npe * 3;
   double* const buf0 = reinterpret_cast<double*>(smem);
-  double* const buf1 = buf0 + tile_doubles;
   const long long n_tiles = (n_elem + eb - 1) / eb;
   const bool aligned = ((uintptr_t)nodes & 15) == 0;
   // a tile goes by bulk copy when its address and size are 16-byte multiples
@@ -109,8 +111,7 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
   };
   auto tile_elems = [&](long long t) { return (int)((t + 1) * eb <= n_elem ? eb : n_elem - t * eb); };
   if (tid == 0) {
-    fr_bar_init(&bar[0]);
-    fr_bar_init(&bar[1]);
+    for (int b = 0; b < FR_STAGES; ++b) fr_bar_init(&bar[b]);
     s_bad = 0;
   }
   if (tid < FR_THREADS / 32) s_ext[tid] = 0.0;
@@ -119,23 +120,29 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
   unsigned phase = 0u;   // bit b: parity of buffer b's next phase
   unsigned issued = 0u;  // bit b: buffer b has a bulk copy outstanding (thread 0's record)
   bool failed = false;
-  if (t < n_tiles && tid == 0 && bulk_ok(t)) {
-    fr_bulk_load(buf0, nodes + t * tile_doubles, (unsigned)(tile_elems(t) * npe * 24), &bar[0]);
-    issued |= 1u;
+  // the first FR_STAGES - 1 tiles of this block
+  for (int j = 0; j < FR_STAGES - 1; ++j) {
+    const long long tj = t + (long long)j * gridDim.x;
+    if (tj < n_tiles && tid == 0 && bulk_ok(tj)) {
+      fr_bulk_load(buf0 + j * tile_doubles, nodes + tj * tile_doubles, (unsigned)(tile_elems(tj) * npe * 24), &bar[j]);
+      issued |= 1u << j;
+    }
   }
   // per element: T_E = FR_THREADS / eb threads (eb <= 128 so T_E >= 2)
   const int te = FR_THREADS / eb;
   double ext_acc = 0.0;
   for (int k = 0; t < n_tiles; ++k, t += gridDim.x) {
-    const int b = k & 1;
-    const long long tn = t + gridDim.x;
+    const int b = k % FR_STAGES;
+    const long long tn = t + (long long)(FR_STAGES - 1) * gridDim.x;
+    const int bn = (k + FR_STAGES - 1) % FR_STAGES;
     if (tn < n_tiles && tid == 0 && bulk_ok(tn)) {
-      // the other buffer was released by the barrier at the end of the last round
-      fr_bulk_load(b ? buf0 : buf1, nodes + tn * tile_doubles, (unsigned)(tile_elems(tn) * npe * 24), &bar[b ^ 1]);
-      issued |= 1u << (b ^ 1);
+      // buffer bn held the tile of the last round, released by its final barrier
+      fr_bulk_load(buf0 + bn * tile_doubles, nodes + tn * tile_doubles, (unsigned)(tile_elems(tn) * npe * 24),
+                   &bar[bn]);
+      issued |= 1u << bn;
     }
     const int ne = tile_elems(t);
-    double* tb = b ? buf1 : buf0;
+    double* tb = buf0 + b * tile_doubles;
     if (bulk_ok(t)) {
       if (fr_bar_wait(&bar[b], (phase >> b) & 1u)) {
         phase ^= 1u << b;
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
     // (bounded), and leave
     if (tid == 0) {
       atomicOr(err, 1);
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < FR_STAGES; ++b)
         if ((issued >> b) & 1u) fr_bar_wait(&bar[b], (phase >> b) & 1u);  // at most one copy per buffer
     }
     return;
@@ -232,7 +239,120 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
   if (tid == 0 && s_bad) atomicOr(bad, 1);
 }
 
+// Element node boxes only, read straight from global memory: a group of
+// FB_GROUP = 4 threads per element, 8 elements per warp.  Thread r of a group
+// reads the element's coordinates r, r + 4, r + 8, ... (every load of a warp
+// covers 32 contiguous bytes of each of its 8 elements), twelve at a time, so
+// that within each twelve its three values fall on the axes r mod 3, r + 1 and
+// r + 2 mod 3 in that order: fixed accumulators, no indexing by axis.  The
+// boxes are taken on integer keys of the FP64 bit patterns, compared as pairs
+// of 32-bit words.
+// No shared memory or barrier: the whole SM's warps keep loads in flight,
+// which is what the sweep (a pure stream over the node array) needs.
+constexpr int FB_GROUP = 4;
+
+// an order-preserving key of a finite double as two 32-bit words (high word
+// signed, low word unsigned, compared in that order): 64-bit integer compares
+// would run on GB300's slow FP64 pipe, 32-bit ones run on the integer pipe
+struct FbKey {
+  int h;
+  unsigned l;
+};
+__device__ __forceinline__ FbKey fb_key(long long b) {
+  int h = (int)(b >> 32);
+  unsigned l = (unsigned)b;
+  const int neg = h >> 31;  // all ones for a negative value: flip its magnitude bits
+  return FbKey{h ^ (neg & 0x7fffffff), l ^ (unsigned)neg};
+}
+__device__ __forceinline__ bool fb_less(FbKey a, FbKey b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ double fb_value(FbKey k) {
+  const int neg = k.h >> 31;
+  const int h = k.h ^ (neg & 0x7fffffff);
+  const unsigned l = k.l ^ (unsigned)neg;
+  return __longlong_as_double(((long long)h << 32) | (long long)l);
+}
+
+__global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ nodes, long long n_elem, int npe,
+                                                    float* __restrict__ box, int* __restrict__ bad,
+                                                    double* __restrict__ ext_sum) {
+  const int lane = threadIdx.x & 31, r = lane & (FB_GROUP - 1);
+  const long long nval = 3LL * npe;
+  // |x| >= 1e300 (or not finite) on the high word, then the low word
+  const int bigh = (int)(__double_as_longlong(1e300) >> 32);
+  const unsigned bigl = (unsigned)__double_as_longlong(1e300);
+  const long long stride = (long long)gridDim.x * (blockDim.x / FB_GROUP);
+  double ext_acc = 0.0;
+  bool nonfinite = false;
+  // the loop runs in step across each warp (its groups' shuffles)
+  for (long long e0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / FB_GROUP; e0 < n_elem;
+       e0 += stride) {
+    const long long e = e0 + (lane >> 2);
+    const bool valid = e < n_elem;
+    const FbKey top{INT_MAX, 0xffffffffu}, bot{INT_MIN, 0u};
+    FbKey lo0 = top, lo1 = top, lo2 = top, hi0 = bot, hi1 = bot, hi2 = bot;
+    if (valid) {
+      const long long* x = reinterpret_cast<const long long*>(nodes) + e * nval;
+#pragma unroll 4
+      for (long long c = 0; c < nval; c += 12) {
+        const long long i0 = c + r, i1 = i0 + 4, i2 = i0 + 8;
+        // past the end a load of x[0] keeps the access in bounds; its value
+        // is not used
+        const long long b0 = __ldg(x + (i0 < nval ? i0 : 0));
+        const long long b1 = __ldg(x + (i1 < nval ? i1 : 0));
+        const long long b2 = __ldg(x + (i2 < nval ? i2 : 0));
+        const bool v0 = i0 < nval, v1 = i1 < nval, v2 = i2 < nval;
+        const long long bb[3] = {b0, b1, b2};
+        const bool vv[3] = {v0, v1, v2};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int mh = (int)(bb[j] >> 32) & 0x7fffffff;
+          const unsigned ml = (unsigned)bb[j];
+          nonfinite |= vv[j] && (mh > bigh || (mh == bigh && ml >= bigl));
+        }
+        const FbKey q0 = fb_key(b0), q1 = fb_key(b1), q2 = fb_key(b2);
+        if (v0) { if (fb_less(q0, lo0)) lo0 = q0; if (fb_less(hi0, q0)) hi0 = q0; }
+        if (v1) { if (fb_less(q1, lo1)) lo1 = q1; if (fb_less(hi1, q1)) hi1 = q1; }
+        if (v2) { if (fb_less(q2, lo2)) lo2 = q2; if (fb_less(hi2, q2)) hi2 = q2; }
+      }
+    }
+    // accumulator j of thread r holds axis (r + j) mod 3: put them in axis order
+    const int m = r % 3;
+    FbKey lo[3], hi[3];
+    lo[0] = m == 0 ? lo0 : (m == 1 ? lo2 : lo1);
+    lo[1] = m == 0 ? lo1 : (m == 1 ? lo0 : lo2);
+    lo[2] = m == 0 ? lo2 : (m == 1 ? lo1 : lo0);
+    hi[0] = m == 0 ? hi0 : (m == 1 ? hi2 : hi1);
+    hi[1] = m == 0 ? hi1 : (m == 1 ? hi0 : hi2);
+    hi[2] = m == 0 ? hi2 : (m == 1 ? hi1 : hi0);
+#pragma unroll
+    for (int s = 1; s < FB_GROUP; s <<= 1)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const FbKey ol{__shfl_xor_sync(0xffffffffu, lo[a].h, s), __shfl_xor_sync(0xffffffffu, lo[a].l, s)};
+        const FbKey oh{__shfl_xor_sync(0xffffffffu, hi[a].h, s), __shfl_xor_sync(0xffffffffu, hi[a].l, s)};
+        if (fb_less(ol, lo[a])) lo[a] = ol;
+        if (fb_less(hi[a], oh)) hi[a] = oh;
+      }
+    if (valid && r == 0) {
+      double ext = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double dl = fb_value(lo[a]), dh = fb_value(hi[a]);
+        box[6 * e + a] = __double2float_rd(dl);
+        box[6 * e + 3 + a] = __double2float_ru(dh);
+        ext = fmax(ext, dh - dl);
+      }
+      if (ext < 1e300) ext_acc += ext;
+    }
+  }
+  if (__any_sync(0xffffffffu, nonfinite) && lane == 0) atomicOr(bad, 1);
+  if (ext_sum) {
+    for (int s = 16; s; s >>= 1) ext_acc += __shfl_xor_sync(0xffffffffu, ext_acc, s);
+    if (lane == 0 && ext_acc > 0.0) atomicAdd(ext_sum, ext_acc);
+  }
+}
+
 // dynamic shared memory of k_elem_frames for elements of npe nodes
-inline size_t frames_smem(int npe) { return (size_t)2 * frames_tile_elems(npe) * npe * 24; }
+inline size_t frames_smem(int npe) { return (size_t)FR_STAGES * frames_tile_elems(npe) * npe * 24; }
 
 }  // namespace dc

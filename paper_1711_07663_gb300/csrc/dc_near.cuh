@@ -602,8 +602,9 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
         bool keep = false;
         int f = 0;
         if (k < total) {
-          f = in.bin_faces[fsrc + (kk - esrc)];
-          const float* fbx = in.fbox + 6 * (long long)f;
+          const int pos = fsrc + (kk - esrc);
+          f = in.bin_faces[pos];
+          const float* fbx = in.bin_fbox + 6 * (long long)pos;
           float bb[6] = {fbx[0], fbx[1], fbx[2], fbx[3], fbx[4], fbx[5]};
           float fm = 0.f;
 #pragma unroll

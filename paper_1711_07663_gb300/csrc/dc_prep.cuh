@@ -313,6 +313,9 @@ __device__ __forceinline__ void bin_fill(Inst* __restrict__ I, const long long* 
   int b = in.fbin[f];
   int pos = in.bin_off[b] + atomicAdd(&in.bin_cnt[b], 1);
   in.bin_faces[pos] = (int)f;
+  // the box beside the id: a search over a bin reads both at once
+#pragma unroll
+  for (int a = 0; a < 6; ++a) in.bin_fbox[6 * (long long)pos + a] = in.fbox[6 * f + a];
 }
 
 // ------------------------------------------------------------------ a3: inside / outside
@@ -596,8 +599,19 @@ __device__ void classify_elem(Inst* __restrict__ I, const long long* __restrict_
               }
             }
           }
-        if (any_near || (any_in && any_out)) cand = true;
-        else flag = any_in ? DC_HOLE_ : DC_FIELD_;
+        if (any_near || (any_in && any_out)) {
+          cand = true;
+          // the exact stage reads every candidate's FP64 nodes next: start
+          // bringing them into L2 now (a hint; 128-byte lines)
+          const int npe = (in.p + 1) * (in.p + 1) * (in.p + 1);
+          const char* nb = reinterpret_cast<const char*>(in.nodes + e * npe * 3);
+          const char* ne = nb + npe * 24;
+          for (const char* a = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(nb) & ~uintptr_t(127)); a < ne;
+               a += 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+        } else {
+          flag = any_in ? DC_HOLE_ : DC_FIELD_;
+        }
       }
     }
     if (!cand) {
@@ -681,16 +695,18 @@ __global__ void __launch_bounds__(256) k_prep(Inst* __restrict__ I, const long l
   pdl_enter();
   const long long* foff = off;
   const long long* eoff = off + n_inst + 1;
+  const long long* toff = off + 2 * (n_inst + 1);   // surface tiles
+  const long long* troff = off + 3 * (n_inst + 1);  // surface triangles
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const long long gwarp = tid >> 5, nwarp = nthr >> 5;
   unsigned k = 0;
-  // a1 + a2: pose and face boxes, SURF_FPB faces per block and step
-  for (int ii = 0; ii < n_inst; ++ii) {
-    Inst& in = I[ii];
-    const long long nt = (in.n_faces + SURF_FPB - 1) / SURF_FPB;
-    for (long long t = blockIdx.x; t < nt; t += gridDim.x) surface_tile(in, t * SURF_FPB, false);
+  // a1 + a2: pose and face boxes, SURF_FPB faces per block and step, the
+  // tiles of every instance spread over the whole grid
+  for (long long t = blockIdx.x; t < toff[n_inst]; t += gridDim.x) {
+    const int ii = find_inst(toff, n_inst, t);
+    surface_tile(I[ii], (t - toff[ii]) * SURF_FPB, false);
   }
   if (!prep_barrier(sync, ++k, sync + 1)) return;
   for (long long ii = tid; ii < n_inst; ii += nthr) grid_from_box(I[ii]);
@@ -704,10 +720,9 @@ __global__ void __launch_bounds__(256) k_prep(Inst* __restrict__ I, const long l
   if (!prep_barrier(sync, ++k, sync + 1)) return;
   // faces into their bins, and the row centre lines' crossings
   for (long long g = tid; g < nf_total; g += nthr) bin_fill(I, foff, n_inst, nf_total, g);
-  for (int ii = 0; ii < n_inst; ++ii) {
-    Inst& in = I[ii];
-    const long long ntri = in.n_faces * 2LL * in.q * in.q;
-    for (long long g = tid; g < ntri; g += nthr) row_cross(in, g);
+  for (long long g = tid; g < troff[n_inst]; g += nthr) {
+    const int ii = find_inst(troff, n_inst, g);
+    row_cross(I[ii], g - troff[ii]);
   }
   if (!prep_barrier(sync, ++k, sync + 1)) return;
   for (int ii = 0; ii < n_inst; ++ii) {

@@ -207,6 +207,9 @@ struct Slot {
 
 // face order the slots' reservation at dc_create is sized for
 constexpr int RESERVE_Q = 2;
+// elements up to which the fused prep kernel also classifies (beyond, a
+// separate k_classify launch does)
+constexpr long long PREP_CLASSIFY_MAX = 1LL << 20;
 // prefix offsets over a batch's instances, each n + 1 long: faces, elements,
 // k_prep's surface tiles, surface triangles
 constexpr int NOFF = 4;
@@ -512,8 +515,14 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     at[0].val.cooperative = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
+    // a batch of millions of elements is classified by its own full-width
+    // launch; a single grid's elements are a phase of the fused kernel
+    const bool fused_classify = ne_total <= PREP_CLASSIFY_MAX;
     CK(cudaLaunchKernelEx(&lc, k_prep, d_inst, (const long long*)d_off, n, nf_total, ne_total, cl, d_cnt,
-                          reinterpret_cast<unsigned*>(d_cnt + 22)));
+                          reinterpret_cast<unsigned*>(d_cnt + 22), fused_classify ? 1 : 0));
+    if (!fused_classify)
+      CK(launch_k(true, k_classify, dim3((unsigned)((ne_total + TB - 1) / TB)), dim3(TB), 0, st, d_inst,
+                  (const long long*)(d_off + n + 1), n, ne_total, cl, d_cnt));
   }
   if (prof) {
     // the three phases are one kernel: their times are reported together

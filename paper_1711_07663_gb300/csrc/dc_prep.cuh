@@ -689,9 +689,13 @@ __device__ bool prep_barrier(unsigned* count, unsigned k, unsigned* timed_out) {
 // the launch and drain of seven small kernels out of the chain.  sync[0]
 // counts barrier arrivals, sync[1] records a barrier that ran out (the cut
 // then reports an internal error).
+// classify = 0: the classification is left to a separate k_classify launch
+// (a batch of millions of elements, which a grid of one launch per SM's
+// worth of threads would step through serially).
 __global__ void __launch_bounds__(256) k_prep(Inst* __restrict__ I, const long long* __restrict__ off, int n_inst,
                                               long long nf_total, long long ne_total, CandList cl,
-                                              unsigned long long* __restrict__ cnt, unsigned* __restrict__ sync) {
+                                              unsigned long long* __restrict__ cnt, unsigned* __restrict__ sync,
+                                              int classify) {
   pdl_enter();
   const long long* foff = off;
   const long long* eoff = off + n_inst + 1;
@@ -730,6 +734,7 @@ __global__ void __launch_bounds__(256) k_prep(Inst* __restrict__ I, const long l
     const long long nrows = (long long)in.dims[1] * in.dims[2];
     for (long long r = gwarp; r < nrows; r += nwarp) row_label(in, (int)r, lane);
   }
+  if (!classify) return;
   if (!prep_barrier(sync, ++k, sync + 1)) return;
   // a4: every element against the map (warps step together for the compaction)
   for (long long base = tid - lane; base < ne_total; base += nthr) classify_elem(I, eoff, n_inst, ne_total, cl, cnt, base + lane);

@@ -5,6 +5,10 @@
 // calls (dc_submit / dc_poll) that let requests in different slots overlap on
 // the GPU.
 #include <cuda_runtime.h>
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define DC_HAVE_NVTX 1
+#endif
 
 #include <algorithm>
 #include <atomic>
@@ -31,6 +35,19 @@ using namespace dc;
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range over a host-side phase of a call (visible in a profiler's
+// timeline; no cost when no tool is attached)
+struct NvtxRange {
+#ifdef DC_HAVE_NVTX
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+#else
+  explicit NvtxRange(const char*) {}
+#endif
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 dc_status fail(dc_status st, const char* fmt, ...) {
   char buf[512];
@@ -603,6 +620,7 @@ dc_status launch_graph(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t s
   for (auto& g : s.graphs)
     if (g.key == P) hit = &g;
   if (!hit) {
+    NvtxRange nr("directcut: capture launch graph");
     if (s.graphs.size() >= 8) {
       auto lru = std::min_element(s.graphs.begin(), s.graphs.end(),
                                   [](const GraphEntry& a, const GraphEntry& b) { return a.last_use < b.last_use; });
@@ -634,6 +652,7 @@ dc_status launch_graph(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t s
 // synchronous calls upload straight from the caller's buffer, which stays
 // valid until they return.
 dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool copy_inputs) {
+  NvtxRange nr("directcut: enqueue");
   const int n = (int)v.size();
   long long nf_total = 0, ne_total = 0, max_tri = 0, max_f = 0;
   int pmax = 1, qmax = 1, pmin = MAX_P, qmin = MAX_Q;
@@ -795,6 +814,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
 // copy results of a finished (synchronised) batch back and turn device error
 // bits into a status; fills ctx->last
 dc_status finish(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st) {
+  NvtxRange nr("directcut: wait and read back");
   const int n = s.n_inst;
   CK(cudaMemcpyAsync(s.h_cnt, s.d_cnt, sizeof(unsigned long long) * NCNT, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s.h_inst, s.d_inst, sizeof(Inst) * n, cudaMemcpyDeviceToHost, st));
@@ -911,6 +931,7 @@ dc_status dc_config_default(dc_config* cfg) {
 
 dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t n_meshes, dc_ctx** out) {
   g_err.clear();
+  NvtxRange nr("directcut: dc_create");
   if (!out) return fail(DC_EINVAL, "out is NULL");
   *out = nullptr;
   dc_config cfg;
@@ -1108,6 +1129,7 @@ static dc_status run_sync(dc_ctx* c, const std::vector<InstReq>& v, bool async_o
 
 dc_status dc_cut(dc_ctx* c, int32_t mesh, const dc_request* req) {
   g_err.clear();
+  NvtxRange nr("directcut: dc_cut");
   if (!c) return fail(DC_EINVAL, "ctx is NULL");
   std::lock_guard<std::mutex> lk(c->mu);
   dc_status rc = validate_req(c, mesh, req);
@@ -1120,6 +1142,7 @@ dc_status dc_cut(dc_ctx* c, int32_t mesh, const dc_request* req) {
 
 dc_status dc_cut_batch(dc_ctx* c, int32_t n, const int32_t* meshes, const dc_request* reqs) {
   g_err.clear();
+  NvtxRange nr("directcut: dc_cut_batch");
   if (!c) return fail(DC_EINVAL, "ctx is NULL");
   if (n < 1 || !meshes || !reqs) return fail(DC_EINVAL, "empty batch");
   std::lock_guard<std::mutex> lk(c->mu);
@@ -1253,6 +1276,7 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* out) {
 
 dc_status dc_submit(dc_ctx* c, int32_t mesh, const dc_request* req, uint64_t* ticket) {
   g_err.clear();
+  NvtxRange nr("directcut: dc_submit");
   if (!c || !ticket) return fail(DC_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lk(c->mu);
   dc_status rc = validate_req(c, mesh, req);

@@ -335,6 +335,18 @@ dc_status dc_unblank(int32_t kind, int64_t n_elem, const int8_t *iblank_prev, co
 /* Library version string. */
 const char *dc_version(void);
 
+/* Allocation accounting and failure injection, for testing the handling of
+ * DC_ENOMEM without exhausting memory.  Every device allocation (cudaMalloc)
+ * and pinned host allocation (cudaMallocHost) the library makes, in any
+ * context or thread, is counted.  after >= 0 arms a one-shot failure: the
+ * allocation `after` allocations from now (0: the next one) reports failure
+ * as if memory were exhausted, and the call that made it returns DC_ENOMEM
+ * after releasing what it holds; the context stays usable.  after < 0
+ * disarms.  Returns the number of allocations made since the library was
+ * loaded (before this call).  Host-side only: no GPU memory is touched and
+ * no device is needed. */
+int64_t dc_fail_alloc(int64_t after);
+
 /* ------------------------------------------------------------------------
  * Point connectivity: donors for receptor points (after the cut)
  * ------------------------------------------------------------------------

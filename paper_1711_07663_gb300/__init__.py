@@ -24,7 +24,7 @@ __all__ = [
     "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats", "dc_destroy",
     "dc_last_error", "dc_version", "dc_cut_noalloc", "Context", "EXPORTED",
     "DC_WALL", "DC_OVERSET", "dc_blank_union", "dc_ab_faces", "dc_unblank", "structured_neighbours",
-    "dc_get_tuning", "dc_set_tuning", "dc_autotune", "PointLocator",
+    "dc_get_tuning", "dc_set_tuning", "dc_autotune", "PointLocator", "dc_fail_alloc",
 ]
 
 DC_OK, DC_PENDING = 0, 1
@@ -35,7 +35,7 @@ DC_FP64, DC_FP32_RECHECK, DC_HEURISTIC = 0, 1, 2
 EXPORTED = ("dc_config_default", "dc_create", "dc_cut", "dc_cut_batch", "dc_submit", "dc_poll", "dc_get_stats",
             "dc_destroy", "dc_last_error", "dc_version", "dc_cut_noalloc", "dc_blank_union", "dc_ab_faces",
             "dc_unblank", "dc_get_tuning", "dc_set_tuning", "dc_autotune", "dc_pc_create", "dc_pc_locate",
-            "dc_pc_get_stats", "dc_pc_destroy")
+            "dc_pc_get_stats", "dc_pc_destroy", "dc_fail_alloc")
 DC_WALL, DC_OVERSET = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -127,6 +127,8 @@ def load(build_if_missing: bool = False):
         L.dc_last_error.restype = ctypes.c_char_p
         L.dc_version.argtypes = []
         L.dc_version.restype = ctypes.c_char_p
+        L.dc_fail_alloc.argtypes = [i64]
+        L.dc_fail_alloc.restype = i64
         L.dc_cut_noalloc.argtypes = [i32, i64, P, i32, i64, P, P, ctypes.c_double, P, P, P]
         L.dc_cut_noalloc.restype = i32
         L.dc_blank_union.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(i32), i64, P, P]
@@ -162,6 +164,13 @@ def dc_last_error(ctx=None) -> str:
 
 def dc_version() -> str:
     return load().dc_version().decode()
+
+
+def dc_fail_alloc(after: int) -> int:
+    """Arm (after >= 0) or disarm (after < 0) a one-shot failure of the
+    library's allocation `after` allocations from now; returns the number of
+    device and pinned-host allocations the library has made so far."""
+    return int(load().dc_fail_alloc(int(after)))
 
 
 def _check(st: int) -> int:

@@ -49,6 +49,35 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Every device and pinned-host allocation of the library goes through
+// dev_alloc / host_alloc: they count allocations, and dc_fail_alloc can arm a
+// one-shot failure of a later one, so that the handling of DC_ENOMEM (by the
+// library and by its callers) can be exercised without exhausting memory.
+std::atomic<long long> g_allocs{0};
+std::atomic<long long> g_fail_at{-1};
+
+bool alloc_fails() {
+  const long long k = g_allocs.fetch_add(1);
+  long long f = g_fail_at.load();
+  return f >= 0 && k == f && g_fail_at.compare_exchange_strong(f, -1);
+}
+template <class T>
+cudaError_t dev_alloc(T** p, size_t n) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), n);
+}
+template <class T>
+cudaError_t host_alloc(T** p, size_t n) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(reinterpret_cast<void**>(p), n);
+}
+
 dc_status fail(dc_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -63,6 +92,15 @@ dc_status fail(dc_status st, const char* fmt, ...) {
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
     if (e_ != cudaSuccess) return fail(DC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+// an allocation: its failure is DC_ENOMEM, and the sticky error is cleared
+#define CKA(call)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      cudaGetLastError();                                                                    \
+      return fail(DC_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_));                       \
+    }                                                                                        \
   } while (0)
 
 // ------------------------------------------------------------------ element boxes
@@ -411,7 +449,7 @@ dc_status ensure_arena(dc_ctx* c, Slot& s, size_t need) {
     s.arena.base = nullptr;
     s.arena.cap = 0;
   }
-  cudaError_t e = cudaMalloc(&s.arena.base, grow);
+  cudaError_t e = dev_alloc(&s.arena.base, grow);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(DC_ENOMEM, "cudaMalloc(%zu) for the cut arena failed: %s", grow, cudaGetErrorString(e));
@@ -434,9 +472,12 @@ dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total, boo
       s.ring_off[r] = nullptr;
       s.ring_used[r] = false;
     }
+    // capacity 0 until every buffer exists: a failed allocation leaves the
+    // ring to be rebuilt by the next call
+    s.h_inst_cap = 0;
     for (int r = 0; r < Slot::RING; ++r) {
-      CK(cudaMallocHost(&s.ring_inst[r], sizeof(Inst) * n_inst));
-      CK(cudaMallocHost(&s.ring_off[r], sizeof(long long) * NOFF * (n_inst + 1)));
+      CKA(host_alloc(&s.ring_inst[r], sizeof(Inst) * n_inst));
+      CKA(host_alloc(&s.ring_off[r], sizeof(long long) * NOFF * (n_inst + 1)));
     }
     s.h_inst_cap = n_inst;
   }
@@ -449,17 +490,19 @@ dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total, boo
     s.ring_used[r] = false;
     s.cur_ring = r;
   }
-  if (!s.h_cnt) CK(cudaMallocHost(&s.h_cnt, sizeof(unsigned long long) * NCNT));
+  if (!s.h_cnt) CKA(host_alloc(&s.h_cnt, sizeof(unsigned long long) * NCNT));
   if ((long long)s.h_out_cap < ne_total) {
     host_free(c, s.h_flags);
     s.h_flags = nullptr;
-    CK(cudaMallocHost(&s.h_flags, (size_t)ne_total));
+    s.h_out_cap = 0;
+    CKA(host_alloc(&s.h_flags, (size_t)ne_total));
     s.h_out_cap = (size_t)ne_total;
   }
   if (want_host_dist && (long long)s.h_dist_cap < ne_total) {
     host_free(c, s.h_dist);
     s.h_dist = nullptr;
-    CK(cudaMallocHost(&s.h_dist, sizeof(double) * ne_total));
+    s.h_dist_cap = 0;
+    CKA(host_alloc(&s.h_dist, sizeof(double) * ne_total));
     s.h_dist_cap = (size_t)ne_total;
   }
   return DC_OK;
@@ -471,7 +514,7 @@ dc_status ensure_face_stage(dc_ctx* c, Slot& s, size_t n) {
   host_free(c, s.h_faces);
   s.h_faces = nullptr;
   s.h_faces_cap = 0;
-  if (cudaMallocHost(&s.h_faces, sizeof(double) * n) != cudaSuccess) {
+  if (host_alloc(&s.h_faces, sizeof(double) * n) != cudaSuccess) {
     cudaGetLastError();
     return fail(DC_ENOMEM, "cudaMallocHost(%zu) for the face staging failed", sizeof(double) * n);
   }
@@ -916,6 +959,12 @@ const char* dc_last_error(const dc_ctx* ctx) {
 
 const char* dc_version(void) { return "directcut 0.1 (sm_103a)"; }
 
+int64_t dc_fail_alloc(int64_t after) {
+  const long long n = g_allocs.load();
+  g_fail_at.store(after >= 0 ? n + after : -1);
+  return n;
+}
+
 dc_status dc_config_default(dc_config* cfg) {
   if (!cfg) return fail(DC_EINVAL, "cfg is NULL");
   memset(cfg, 0, sizeof(*cfg));
@@ -1010,7 +1059,7 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     if (st) return bail(st);
   }
   int* d_bad = nullptr;  // [0]: a node is not finite; bytes 8..15: sum of element extents
-  if (cudaMalloc(&d_bad, 16) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  if (dev_alloc(&d_bad, 16) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
   double* d_ext = reinterpret_cast<double*>(reinterpret_cast<char*>(d_bad) + 8);
   cudaStream_t st = c->slots[0].stream;
   c->meshes.resize(n_meshes);
@@ -1026,7 +1075,7 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
       cudaFree(d_bad);
       return bail(fail(DC_ENOMEM, "mesh %d does not fit the memory budget", i));
     }
-    if (cudaMalloc(&m.nodes, nb) != cudaSuccess || cudaMalloc(&m.box, bb) != cudaSuccess) {
+    if (dev_alloc(&m.nodes, nb) != cudaSuccess || dev_alloc(&m.box, bb) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(d_bad);
       return bail(fail(DC_ENOMEM, "mesh %d: cudaMalloc of %zu bytes failed", i, nb + bb));
@@ -1038,7 +1087,7 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
       return bail(fail(DC_ECUDA, "mesh %d: copying nodes failed", i));
     }
     cudaMemsetAsync(d_bad, 0, 16, st);
-    k_elem_boxes<<<(unsigned)std::min<long long>((md.n_elem + 63) / 64, (long long)c->n_sm * 8), 256, 0, st>>>(
+    k_elem_boxes<<<fb_grid(md.n_elem, c->n_sm), 256, 0, st>>>(
         m.nodes, md.n_elem, (int)npe, m.box, d_bad, d_ext);
     const cudaError_t fe = cudaGetLastError();
     int bad[2] = {0, 0};
@@ -1078,12 +1127,12 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     size_t host_total = 0;
     for (size_t i = 0; i < n_slots; ++i) host_total += host_need(i);
     if (!cfg.mem_budget_bytes || c->mesh_bytes + need * n_slots <= cfg.mem_budget_bytes) {
-      if (cudaMalloc(&c->dev_block, need * n_slots) != cudaSuccess) {
+      if (dev_alloc(&c->dev_block, need * n_slots) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(DC_ENOMEM, "cudaMalloc(%zu) for the slots' arenas failed", need * n_slots));
       }
       c->dev_bytes = need * n_slots;
-      if (cudaMallocHost(&c->pin_block, host_total) != cudaSuccess) {
+      if (host_alloc(&c->pin_block, host_total) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(DC_ENOMEM, "cudaMallocHost(%zu) for the slots' staging failed", host_total));
       }
@@ -1522,7 +1571,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CKQ(cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
   CKQ(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * NCNT, st));
   CKQ(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
-  k_elem_boxes<<<(unsigned)std::min<long long>((n_elem + 63) / 64, (long long)D.n_sm * 8), 256, 0, st>>>(
+  k_elem_boxes<<<fb_grid(n_elem, D.n_sm), 256, 0, st>>>(
       nodes, n_elem, npe, ebox, d_bad, nullptr);
   unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
   k_surface<<<dim3((unsigned)((n_faces + SURF_FPB - 1) / SURF_FPB), 1), TB, 0, st>>>(d_inst);
@@ -1569,8 +1618,13 @@ dc_status ov_counter(unsigned long long** out) {
   return DC_OK;
 }
 
+// blocks of 256 threads for n elements: at most 16 per SM of the current device
 unsigned ov_grid(long long n) {
-  return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n_sm < 1)
+    n_sm = 1;
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)n_sm * 16));
 }
 
 }  // namespace
@@ -1729,11 +1783,11 @@ dc_status pc_reserve(dc_pc* pc, size_t n) {
   pc->ncand = pc->cand = nullptr;
   pc->donor = nullptr;
   pc->cap = 0;
-  if (cudaMalloc(&pc->pts, sizeof(double) * 3 * m) != cudaSuccess ||
-      cudaMalloc(&pc->xloc, sizeof(double) * 3 * m) != cudaSuccess ||
-      cudaMalloc(&pc->ref, sizeof(double) * 3 * m) != cudaSuccess || cudaMalloc(&pc->ncand, sizeof(int) * m) != cudaSuccess ||
-      cudaMalloc(&pc->cand, sizeof(int) * PC_CAND * m) != cudaSuccess ||
-      cudaMalloc(&pc->donor, sizeof(long long) * m) != cudaSuccess)
+  if (dev_alloc(&pc->pts, sizeof(double) * 3 * m) != cudaSuccess ||
+      dev_alloc(&pc->xloc, sizeof(double) * 3 * m) != cudaSuccess ||
+      dev_alloc(&pc->ref, sizeof(double) * 3 * m) != cudaSuccess || dev_alloc(&pc->ncand, sizeof(int) * m) != cudaSuccess ||
+      dev_alloc(&pc->cand, sizeof(int) * PC_CAND * m) != cudaSuccess ||
+      dev_alloc(&pc->donor, sizeof(long long) * m) != cudaSuccess)
     return fail(DC_ENOMEM, "point scratch for %zu points: cudaMalloc failed", m);
   pc->cap = m;
   return DC_OK;
@@ -1798,14 +1852,14 @@ dc_status dc_pc_create(int32_t device, int32_t p, int64_t n_elem, const double* 
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return bail(fail(DC_ECUDA, "cudaGetDeviceProperties failed"));
   pc->n_sm = prop.multiProcessorCount;
   if (cudaStreamCreateWithFlags(&pc->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&pc->nodes, sizeof(double) * nn) != cudaSuccess ||
-      cudaMalloc(&pc->loc, sizeof(float) * nn) != cudaSuccess ||
-      cudaMalloc(&pc->org, sizeof(double) * 3 * n_elem) != cudaSuccess ||
-      cudaMalloc(&pc->fbox, sizeof(float) * 6 * n_elem) != cudaSuccess ||
-      cudaMalloc(&pc->ebox, sizeof(double) * 6 * n_elem) != cudaSuccess ||
-      cudaMalloc(&pc->h, sizeof(float) * n_elem) != cudaSuccess ||
-      cudaMalloc(&pc->tree, sizeof(PcNode) * T.size()) != cudaSuccess ||
-      cudaMalloc(&pc->cnt, sizeof(unsigned long long) * 4) != cudaSuccess)
+      dev_alloc(&pc->nodes, sizeof(double) * nn) != cudaSuccess ||
+      dev_alloc(&pc->loc, sizeof(float) * nn) != cudaSuccess ||
+      dev_alloc(&pc->org, sizeof(double) * 3 * n_elem) != cudaSuccess ||
+      dev_alloc(&pc->fbox, sizeof(float) * 6 * n_elem) != cudaSuccess ||
+      dev_alloc(&pc->ebox, sizeof(double) * 6 * n_elem) != cudaSuccess ||
+      dev_alloc(&pc->h, sizeof(float) * n_elem) != cudaSuccess ||
+      dev_alloc(&pc->tree, sizeof(PcNode) * T.size()) != cudaSuccess ||
+      dev_alloc(&pc->cnt, sizeof(unsigned long long) * 4) != cudaSuccess)
     return bail(fail(DC_ENOMEM, "donor grid of %lld elements: cudaMalloc failed", (long long)n_elem));
   cudaStream_t st = pc->stream;
   if (cudaMemcpyAsync(pc->nodes, nodes, sizeof(double) * nn,
@@ -1815,7 +1869,7 @@ dc_status dc_pc_create(int32_t device, int32_t p, int64_t n_elem, const double* 
       cudaMemcpyAsync(pc->tree, T.data(), sizeof(PcNode) * T.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return bail(fail(DC_ECUDA, "uploading the donor grid failed"));
   int* d_bad = nullptr;
-  if (cudaMalloc(&d_bad, 2 * sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
+  if (dev_alloc(&d_bad, 2 * sizeof(int)) != cudaSuccess) return bail(fail(DC_ENOMEM, "cudaMalloc failed"));
   cudaMemsetAsync(d_bad, 0, 2 * sizeof(int), st);
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);

@@ -22,6 +22,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <limits.h>
 #include <stdint.h>
 
@@ -248,7 +250,9 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
 // boxes are taken on integer keys of the FP64 bit patterns, compared as pairs
 // of 32-bit words.
 // No shared memory or barrier: the whole SM's warps keep loads in flight,
-// which is what the sweep (a pure stream over the node array) needs.
+// which is what the sweep (a pure stream over the node array) needs.  The
+// grid is one wave (fb_grid): the loop strides over the elements, so no SM
+// idles through a partial second wave.
 constexpr int FB_GROUP = 4;
 
 // an order-preserving key of a finite double as two 32-bit words (high word
@@ -276,7 +280,9 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
                                                     float* __restrict__ box, int* __restrict__ bad,
                                                     double* __restrict__ ext_sum) {
   const int lane = threadIdx.x & 31, r = lane & (FB_GROUP - 1);
-  const long long nval = 3LL * npe;
+  // in-element indices are 32-bit: GB300 runs 64-bit integer compares on its
+  // slow FP64 pipe
+  const int nval = 3 * npe;
   // |x| >= 1e300 (or not finite) on the high word, then the low word
   const int bigh = (int)(__double_as_longlong(1e300) >> 32);
   const unsigned bigl = (unsigned)__double_as_longlong(1e300);
@@ -293,8 +299,8 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
     if (valid) {
       const long long* x = reinterpret_cast<const long long*>(nodes) + e * nval;
 #pragma unroll 4
-      for (long long c = 0; c < nval; c += 12) {
-        const long long i0 = c + r, i1 = i0 + 4, i2 = i0 + 8;
+      for (int c = 0; c < nval; c += 12) {
+        const int i0 = c + r, i1 = i0 + 4, i2 = i0 + 8;
         // past the end a load of x[0] keeps the access in bounds; its value
         // is not used
         const long long b0 = __ldg(x + (i0 < nval ? i0 : 0));
@@ -350,6 +356,14 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
     for (int s = 16; s; s >>= 1) ext_acc += __shfl_xor_sync(0xffffffffu, ext_acc, s);
     if (lane == 0 && ext_acc > 0.0) atomicAdd(ext_sum, ext_acc);
   }
+}
+
+// k_elem_boxes' grid: one wave of resident blocks of 256 threads (no more
+// blocks than 64-element groups)
+inline unsigned fb_grid(long long n_elem, int n_sm) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_elem_boxes, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+  return (unsigned)std::max<long long>(1, std::min<long long>((n_elem + 63) / 64, (long long)n_sm * occ));
 }
 
 // dynamic shared memory of k_elem_frames for elements of npe nodes

@@ -24,7 +24,7 @@ def lib():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(dc_[a-z_]+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dc_[a-z_]+)\s*\(", src, flags=re.M)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -40,6 +40,33 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_error_without_gpu(lib):
     assert "sm_103a" in dc.dc_version()
     assert isinstance(dc.dc_last_error(), str)
+
+
+def test_allocation_counter_and_failure_arming_without_gpu(lib):
+    n0 = dc.dc_fail_alloc(-1)
+    assert n0 >= 0
+    # arming and disarming make no allocation
+    assert dc.dc_fail_alloc(0) == n0
+    assert dc.dc_fail_alloc(5) == n0
+    assert dc.dc_fail_alloc(-1) == n0
+    # without a device, dc_create fails before its first allocation
+    cfg = dc.dc_config()
+    dc.load().dc_config_default(ctypes.byref(cfg))
+    if not _has_device():
+        nodes = (ctypes.c_double * 24)()
+        md = dc.dc_mesh_desc(p=1, n_elem=1, nodes=ctypes.cast(nodes, ctypes.c_void_p), nodes_on_device=0)
+        out = ctypes.c_void_p()
+        st = dc.load().dc_create(ctypes.byref(cfg), ctypes.byref(md), 1, ctypes.byref(out))
+        assert st != 0 and not out.value
+        assert dc.dc_fail_alloc(-1) == n0
+
+
+def _has_device():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
 
 
 def test_struct_layouts_match_header(tmp_path):

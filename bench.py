@@ -57,9 +57,9 @@ FLOPS_PER_KEY = 83.0
 # Jacobian (27 x 32), the 1-D bases (72) and the 3x3 solve (60)
 FLOPS_PER_NEWTON_STEP_Q2 = 996.0
 # DRAM bytes (read + write) of one k_near_main launch at the scale workload,
-# from the ncu capture summarised in profiles/k_near_main_scale64.md
-# (8.365568 MB read + 0.408832 MB written); None once the kernel changes
-K_NEAR_MAIN_TRAFFIC = 8_774_400
+# from the ncu capture summarised in profiles/k_near_main_scale64.md; None
+# until the current kernel has been captured
+K_NEAR_MAIN_TRAFFIC = None
 # resident-mesh bytes one cut must move: a FP32 box read and a flag written per
 # element, the FP64 nodes of each element that needs the exact test (Q2: 27
 # nodes x 3 x 8 B; its frame is formed from them), the FP64 face nodes (Q2:

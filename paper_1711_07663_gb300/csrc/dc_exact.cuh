@@ -188,8 +188,10 @@ __device__ __forceinline__ T orient_cert(V3<T> a, V3<T> b, V3<T> c, V3<T> d, T r
 // the FP64 input): P and Q strictly on opposite sides of the plane and the line
 // PQ strictly inside the three edges, each signed volume exceeding its bound.
 // Then the FP64 triangles intersect and their distance is exactly 0.
+// (certified_cross_inl: the same test inlined, for callers whose live
+// registers would otherwise be saved and restored around the call)
 template <class T>
-__device__ __noinline__ bool certified_cross(V3<T> P, V3<T> Q, V3<T> t0, V3<T> t1, V3<T> t2, T rho) {
+__device__ __forceinline__ bool certified_cross_inl(V3<T> P, V3<T> Q, V3<T> t0, V3<T> t1, V3<T> t2, T rho) {
   T b1, b2, c1, c2, c3;
   T o1 = orient_cert(t0, t1, t2, P, rho, b1);
   T o2 = orient_cert(t0, t1, t2, Q, rho, b2);
@@ -198,6 +200,10 @@ __device__ __noinline__ bool certified_cross(V3<T> P, V3<T> Q, V3<T> t0, V3<T> t
   T s2 = orient_cert(P, Q, t1, t2, rho, c2);
   T s3 = orient_cert(P, Q, t2, t0, rho, c3);
   return (s1 > c1 && s2 > c2 && s3 > c3) || (s1 < -c1 && s2 < -c2 && s3 < -c3);
+}
+template <class T>
+__device__ __noinline__ bool certified_cross(V3<T> P, V3<T> Q, V3<T> t0, V3<T> t1, V3<T> t2, T rho) {
+  return certified_cross_inl<T>(P, Q, t0, t1, t2, rho);
 }
 
 // ------------------------------------------------------------------ per-warp scratch

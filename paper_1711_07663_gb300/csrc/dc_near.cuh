@@ -77,34 +77,34 @@ __device__ __forceinline__ bool near_separated(const V3<float>* A, const V3<floa
   return sa || sb;
 }
 
-// The crossing tests of the triangle-triangle test, branch-free: the first
-// edge found (in the test's order) is certified for the exact triangles.
-// True if the pair certainly crosses (its element is fringe).
-__device__ __noinline__ bool near_cross(const V3<float>* a, const V3<float>* b, float S) {
+// The crossing tests of the triangle-triangle test without divisions: an
+// edge PQ whose end points lie strictly on opposite sides of the other
+// triangle's plane crosses it when the three signed volumes of PQ with the
+// triangle's edges share a strict sign.  The first such edge (in the test's
+// order) is certified for the exact triangles.  True if the pair certainly
+// crosses (its element is fringe).
+__device__ __forceinline__ bool edge_through(V3<float> P, V3<float> Q, const V3<float>* t) {
+  const V3<float> d = Q - P, e0 = t[0] - P, e1 = t[1] - P, e2 = t[2] - P;
+  const float o0 = dot(cross(d, e0), e1), o1 = dot(cross(d, e1), e2), o2 = dot(cross(d, e2), e0);
+  return (o0 > 0.f && o1 > 0.f && o2 > 0.f) || (o0 < 0.f && o1 < 0.f && o2 < 0.f);
+}
+__device__ __forceinline__ bool near_cross(const V3<float>* a, const V3<float>* b, float S) {
   const float rho = 2.0f * Eps<float>::u * S;
   const V3<float> na = cross(a[1] - a[0], a[2] - a[0]), nb = cross(b[1] - b[0], b[2] - b[0]);
   float sb[3], sa[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) { sb[j] = dot(na, b[j] - a[0]); sa[j] = dot(nb, a[j] - b[0]); }
-  const bool sepB = (sb[0] > 0.f && sb[1] > 0.f && sb[2] > 0.f) || (sb[0] < 0.f && sb[1] < 0.f && sb[2] < 0.f);
-  const bool sepA = (sa[0] > 0.f && sa[1] > 0.f && sa[2] > 0.f) || (sa[0] < 0.f && sa[1] < 0.f && sa[2] < 0.f);
-  const bool nosep = !sepA && !sepB;
   int xc = -1;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const int k = (j + 1) % 3;
-    {
-      const float s0 = sb[j], s1 = sb[k];
-      const bool c = nosep && ((s0 <= 0.f && s1 >= 0.f) || (s0 >= 0.f && s1 <= 0.f)) && s0 != s1;
-      const V3<float> X = b[j] + (s0 / (c ? s0 - s1 : 1.f)) * (b[k] - b[j]);
-      if (xc < 0 && c && in_tri(X, a[0], a[1], a[2], na)) xc = j;
-    }
-    {
-      const float s0 = sa[j], s1 = sa[k];
-      const bool c = nosep && ((s0 <= 0.f && s1 >= 0.f) || (s0 >= 0.f && s1 <= 0.f)) && s0 != s1;
-      const V3<float> X = a[j] + (s0 / (c ? s0 - s1 : 1.f)) * (a[k] - a[j]);
-      if (xc < 0 && c && in_tri(X, b[0], b[1], b[2], nb)) xc = 3 + j;
-    }
+    if (xc < 0 && ((sb[j] > 0.f && sb[k] < 0.f) || (sb[j] < 0.f && sb[k] > 0.f)) && edge_through(b[j], b[k], a)) xc = j;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int k = (j + 1) % 3;
+    if (xc < 0 && ((sa[j] > 0.f && sa[k] < 0.f) || (sa[j] < 0.f && sa[k] > 0.f)) && edge_through(a[j], a[k], b))
+      xc = 3 + j;
   }
   if (__any_sync(__activemask(), xc >= 0)) {
     // one uniform call: lanes without a crossing certify a dummy and ignore it
@@ -170,6 +170,10 @@ __device__ double tritri64_warp(const V3<double>* a, const V3<double>* b, int la
 // shared memory of one warp of k_near_main
 constexpr int NEAR_UCAP = 32;  // undecided pairs a warp holds for its element
 
+// a warp's counts of one launch, in its shared region (lane 0 keeps them)
+enum { NW_FS, NW_FRINGE, NW_HOLE, NW_FIELD, NW_FACES, NW_PAIRS, NW_FULL, NW_RE, NW_N };
+
+
 // The undecided pairs a warp holds for its element (nul <= 32, lane k takes
 // pair k): the FP32 bounds of the compact triangle test, then the FP64 test
 // (warp-parallel) for each pair those cannot clear.  True if a pair comes
@@ -177,7 +181,7 @@ constexpr int NEAR_UCAP = 32;  // undecided pairs a warp holds for its element
 __device__ __noinline__ bool near_settle(const Inst& in, long long e, const double* eo, const float* en,
                                          const int2* ul, int nul, const unsigned char (*s_et)[MAX_NTE][3],
                                          const unsigned char (*s_ft)[MAX_NTF][3], int lane,
-                                         unsigned long long& n_full, unsigned long long& n_re) {
+                                         unsigned* wc) {
   const unsigned FULL = 0xffffffffu;
   const int p = in.p, q = in.q, npe = (p + 1) * (p + 1) * (p + 1), npf = (q + 1) * (q + 1);
   const float tolf = in.tol_f;
@@ -205,7 +209,7 @@ __device__ __noinline__ bool near_settle(const Inst& in, long long e, const doub
     tritri<float, false>(A, B, U, L, ca, cb, xc);
     open = L - (float)C_SIGMA * Eps<float>::u * S <= tolf;
   }
-  n_full += (unsigned long long)nul;
+  if (lane == 0) wc[NW_FULL] += (unsigned)nul;
   unsigned m64 = __ballot_sync(FULL, open);
   while (m64) {
     const int src = __ffs(m64) - 1;
@@ -221,7 +225,7 @@ __device__ __noinline__ bool near_settle(const Inst& in, long long e, const doub
       b[c] = mkv(fn64[3 * nj] - eo[0], fn64[3 * nj + 1] - eo[1], fn64[3 * nj + 2] - eo[2]);
     }
     const double d = tritri64_warp(a, b, lane);
-    n_re += (lane == 0);
+    if (lane == 0) wc[NW_RE] += 1u;
     if (d <= in.tol) return true;
   }
   return false;
@@ -230,8 +234,12 @@ __device__ __noinline__ bool near_settle(const Inst& in, long long e, const doub
 // faces of one candidate tested together (their nodes are loaded at once)
 constexpr int NEAR_FB = 8;
 
+// faces gathered for one candidate before its batches run (more wait for the
+// next gathering round)
+constexpr int NEAR_FLCAP = 64;
+
 struct NearLayout {
-  int en, eb, fid, ffb, fn, fb, ci, pq, ul, total;
+  int en, eb, fl, ffb, fn, fb, ci, pq, ul, wc, total;
 };
 __host__ __device__ constexpr NearLayout near_layout(int pmax, int qmax) {
   const int npe = (pmax + 1) * (pmax + 1) * (pmax + 1), nte = 12 * pmax * pmax;
@@ -240,13 +248,14 @@ __host__ __device__ constexpr NearLayout near_layout(int pmax, int qmax) {
   int o = 0;
   L.en = o; o = align16(o + 3 * npe * 4);              // element nodes, frame coordinates (x, y, z blocks)
   L.eb = o; o = align16(o + 6 * nte * 4);              // element triangle boxes [6][nte]
-  L.fid = o; o = align16(o + NEAR_FB * 4);             // faces of the batch
+  L.fl = o; o = align16(o + NEAR_FLCAP * 4);          // gathered faces (a batch is a run of NEAR_FB of them)
   L.ffb = o; o = align16(o + NEAR_FB * 8 * 4);         // their boxes in the frame (lo, hi)
   L.fn = o; o = align16(o + NEAR_FB * 3 * npf * 4);    // their nodes in the frame [face][x|y|z][node]
   L.fb = o; o = align16(o + NEAR_FB * 6 * ntf * 4);    // their triangle boxes [face][6][ntf]
   L.ci = o; o = align16(o + 32 * 4);                   // near (face, element triangle) of a chunk
   L.pq = o; o = align16(o + 64 * 4);                   // queued pairs (face << 16 | te << 8 | ts)
   L.ul = o; o = align16(o + NEAR_UCAP * 8);            // undecided pairs (face id, te | ts << 16)
+  L.wc = o; o = align16(o + NW_N * 4);                 // the warp's counts
   L.total = o;
   return L;
 }
@@ -277,13 +286,15 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const NearLayout Lo = FIXED ? near_layout(P, Q) : near_layout(pmax, qmax);
   unsigned char* ws = smem + (size_t)wid * Lo.total;
-  unsigned long long n_fs = 0;
+  unsigned* const wc = reinterpret_cast<unsigned*>(ws + Lo.wc);
+  if ((threadIdx.x & 31) < NW_N) wc[threadIdx.x & 31] = 0u;
+  __syncwarp();
   // a candidate that needs the full per-element search (distances requested,
   // or no node labelled and not fringe) goes to the exact kernels' list;
   // k_exact runs right after this kernel
   auto full_one = [&](unsigned long long ent) {
-    n_fs++;
     if (lane == 0) {
+      wc[NW_FS] += 1u;
       const unsigned long long pos = atomicAdd(&full.count[0], 1ull);
       if (pos < full.cap) full.cand[pos] = ent;
     }
@@ -291,7 +302,8 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   };
   float* en = reinterpret_cast<float*>(ws + Lo.en);
   float* eb = reinterpret_cast<float*>(ws + Lo.eb);
-  int* fid = reinterpret_cast<int*>(ws + Lo.fid);
+  int* const fl = reinterpret_cast<int*>(ws + Lo.fl);
+  int* fid = fl;  // the faces of the current batch
   float* ffb = reinterpret_cast<float*>(ws + Lo.ffb);
   float* fnl = reinterpret_cast<float*>(ws + Lo.fn);
   float* fb = reinterpret_cast<float*>(ws + Lo.fb);
@@ -300,8 +312,6 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
   int2* ul = reinterpret_cast<int2*>(ws + Lo.ul);
   const unsigned long long ncand = ucount(cl.count, cl.cap);
   // per-warp counts of one launch (32 bits suffice)
-  unsigned n_fringe = 0, n_hole = 0, n_field = 0, n_faces = 0, n_pairs = 0;
-  unsigned long long n_full = 0, n_re = 0;
   unsigned long long w = 0, wend = 0;
   while (true) {
     // candidates are taken from a shared cursor, cpw at a time: their costs
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     if (any_in && any_out) {
       // nodes on both sides: the closed element boundary crosses the surface
       if (lane == 0) in.flags[e] = DC_FRINGE_;
-      n_fringe += (lane == 0);
+      if (lane == 0) wc[NW_FRINGE] += 1u;
       continue;
     }
     const float Se = smax, tolf = in.tol_f;
@@ -421,7 +431,7 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     // then FP64 (warp-parallel) for what they cannot clear
     auto settle = [&]() {
       __syncwarp();
-      if (near_settle(in, e, eo, en, ul, nul, s_et, s_ft, lane, n_full, n_re)) fringe = true;
+      if (near_settle(in, e, eo, en, ul, nul, s_et, s_ft, lane, wc)) fringe = true;
       nul = 0;
       __syncwarp();
     };
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
         }
         need = !near_separated(A, B, S, tolf);
       }
-      n_pairs += (unsigned)n;
+      if (lane == 0) wc[NW_PAIRS] += (unsigned)n;
       if (need) crossed = near_cross(A, B, S);
       if (__any_sync(FULL, crossed)) {
         fringe = true;
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     // within tol and their triangle pairs
     auto run_batch = [&]() {
       if (!have_eb) { make_eb(); have_eb = true; }
-      n_faces += (unsigned)nbf;
+      if (lane == 0) wc[NW_FACES] += (unsigned)nbf;
       const int per = 3 * npf;
       // nodes of every face of the batch into the frame; the loads of all of
       // them are issued before any is used
@@ -572,75 +582,78 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
       nbf = 0;
       __syncwarp();
     };
-    for (int cb = 0; cb < nbins && !fringe; cb += 32) {
-      // up to 32 bins at once: lane j reads bin cb + j, a warp scan numbers
-      // their faces, and the lanes walk the faces in steps of 32
-      const int j = cb + lane;
-      int bf0 = 0, bcnt = 0;
-      if (j < nbins) {
-        const int bx = b0[0] + j % nbx, by = b0[1] + (j / nbx) % nby, bz = b0[2] + j / (nbx * nby);
-        const int bi = (bz * in.bdims[1] + by) * in.bdims[0] + bx;
-        bf0 = in.bin_off[bi];
-        bcnt = in.bin_off[bi + 1] - bf0;
-      }
-      int incl = bcnt;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += v;
-      }
-      const int excl = incl - bcnt, total = __shfl_sync(FULL, incl, 31);
-      for (int base = 0; base < total && !fringe; base += 32) {
-        const int k = base + lane, kk = min(k, total - 1);
-        int src = 0;
-#pragma unroll
-        for (int step = 16; step; step >>= 1) {
-          const int c = src + step;
-          if (__shfl_sync(FULL, excl, c) <= kk) src = c;
+    // gather the faces of up to 32 bins at a time into the face list (lane j
+    // reads bin cb + j, a warp scan numbers their faces, the lanes walk the
+    // faces in steps of 32), then run the list's batches; a list that fills
+    // up is tested before gathering resumes where it stopped
+    int cb = 0, kbase = 0;
+    while (cb < nbins && !fringe) {
+      int nfl = 0;
+      while (cb < nbins) {
+        const int j = cb + lane;
+        int bf0 = 0, bcnt = 0;
+        if (j < nbins) {
+          const int bx = b0[0] + j % nbx, by = b0[1] + (j / nbx) % nby, bz = b0[2] + j / (nbx * nby);
+          const int bi = (bz * in.bdims[1] + by) * in.bdims[0] + bx;
+          bf0 = in.bin_off[bi];
+          bcnt = in.bin_off[bi + 1] - bf0;
         }
-        const int fsrc = __shfl_sync(FULL, bf0, src), esrc = __shfl_sync(FULL, excl, src);
-        bool keep = false;
-        int f = 0;
-        if (k < total) {
-          const int pos = fsrc + (kk - esrc);
-          f = in.bin_faces[pos];
-          const float* fbx = in.bin_fbox + 6 * (long long)pos;
-          float bb[6] = {fbx[0], fbx[1], fbx[2], fbx[3], fbx[4], fbx[5]};
-          float fm = 0.f;
+        int incl = bcnt;
 #pragma unroll
-          for (int a = 0; a < 6; ++a) fm = fmaxf(fm, fabsf(bb[a]));
-          float lb = box_dist<float>(gbox[0], gbox[1], gbox[2], gbox[3], gbox[4], gbox[5], bb[0], bb[1], bb[2],
-                                     bb[3], bb[4], bb[5]);
-          lb -= 8.0f * 5.9604645e-8f * fmaxf(gmax, fm);  // rounding of the float box distance
-          keep = lb <= tolf;
+        for (int d = 1; d < 32; d <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, d);
+          if (lane >= d) incl += v;
         }
-        // the kept faces join the batch in lane order; a full batch is tested
-        unsigned fm_ = __ballot_sync(FULL, keep);
-        while (fm_ && !fringe) {
-          const int take = min(__popc(fm_), NEAR_FB - nbf);
-          unsigned sel = 0, mm = fm_;
-          for (int i = 0; i < take; ++i) {
-            sel |= mm & (0u - mm);
-            mm &= mm - 1u;
+        const int excl = incl - bcnt, total = __shfl_sync(FULL, incl, 31);
+        for (; kbase < total && nfl <= NEAR_FLCAP - 32; kbase += 32) {
+          const int k = kbase + lane, kk = min(k, total - 1);
+          int src = 0;
+#pragma unroll
+          for (int step = 16; step; step >>= 1) {
+            const int c = src + step;
+            if (__shfl_sync(FULL, excl, c) <= kk) src = c;
           }
-          if ((sel >> lane) & 1u) fid[nbf + __popc(sel & ((1u << lane) - 1u))] = f;
-          fm_ &= ~sel;
-          nbf += take;
-          __syncwarp();
-          if (nbf == NEAR_FB) run_batch();
+          const int fsrc = __shfl_sync(FULL, bf0, src), esrc = __shfl_sync(FULL, excl, src);
+          bool keep = false;
+          int f = 0;
+          if (k < total) {
+            const int pos = fsrc + (kk - esrc);
+            f = in.bin_faces[pos];
+            const float* fbx = in.bin_fbox + 6 * (long long)pos;
+            float bb[6] = {fbx[0], fbx[1], fbx[2], fbx[3], fbx[4], fbx[5]};
+            float fm = 0.f;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) fm = fmaxf(fm, fabsf(bb[a]));
+            float lb = box_dist<float>(gbox[0], gbox[1], gbox[2], gbox[3], gbox[4], gbox[5], bb[0], bb[1], bb[2],
+                                       bb[3], bb[4], bb[5]);
+            lb -= 8.0f * 5.9604645e-8f * fmaxf(gmax, fm);  // rounding of the float box distance
+            keep = lb <= tolf;
+          }
+          // the kept faces join the list in lane order
+          const unsigned km = __ballot_sync(FULL, keep);
+          if (keep) fl[nfl + __popc(km & ((1u << lane) - 1u))] = f;
+          nfl += __popc(km);
         }
+        if (kbase < total) break;  // the list is full: test it, then resume here
+        cb += 32;
+        kbase = 0;
+      }
+      __syncwarp();
+      for (int s0 = 0; s0 < nfl && !fringe; s0 += NEAR_FB) {
+        fid = fl + s0;
+        nbf = min(NEAR_FB, nfl - s0);
+        run_batch();
       }
     }
-    if (!fringe && nbf > 0) run_batch();
     if (!fringe && nul > 0) settle();
     if (lane == 0) {
       if (fringe) {
         in.flags[e] = DC_FRINGE_;
-        n_fringe++;
+        wc[NW_FRINGE] += 1u;
       } else if (any_in || any_out) {
         in.flags[e] = any_in ? DC_HOLE_ : DC_FIELD_;
-        n_hole += any_in;
-        n_field += !any_in;
+        wc[NW_HOLE] += any_in;
+        wc[NW_FIELD] += !any_in;
       }
     }
     // no label and not fringe: the side needs the full search
@@ -648,7 +661,8 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     __syncwarp();
   }
   if (lane == 0) {
-    if (n_fs) atomicAdd(&nb.cnt[3], n_fs);
+    const unsigned n_fringe = wc[NW_FRINGE], n_hole = wc[NW_HOLE], n_field = wc[NW_FIELD], n_faces = wc[NW_FACES];
+    if (wc[NW_FS]) atomicAdd(&nb.cnt[3], (unsigned long long)wc[NW_FS]);
     if (n_fringe | n_hole | n_field) {
       atomicAdd(&gcnt[3], (unsigned long long)n_fringe);
       atomicAdd(&gcnt[4], (unsigned long long)n_hole);
@@ -657,9 +671,9 @@ __global__ void __launch_bounds__(NEAR_MAX_WARPS * 32, 1)
     if (n_faces) {
       atomicAdd(&nb.cnt[0], (unsigned long long)n_faces);
       atomicAdd(&gcnt[0], (unsigned long long)n_faces);
-      atomicAdd(&gcnt[1], (unsigned long long)n_pairs);
-      atomicAdd(&nb.cnt[5], n_full);
-      atomicAdd(&gcnt[2], n_re);
+      atomicAdd(&gcnt[1], (unsigned long long)wc[NW_PAIRS]);
+      atomicAdd(&nb.cnt[5], (unsigned long long)wc[NW_FULL]);
+      atomicAdd(&gcnt[2], (unsigned long long)wc[NW_RE]);
     }
   }
 }

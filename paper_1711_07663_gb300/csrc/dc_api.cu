@@ -1573,7 +1573,7 @@ extern "C" dc_status dc_cut_noalloc(int32_t p, int64_t n_elem, const double* nod
   CKQ(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
   k_elem_boxes<<<fb_grid(n_elem, D.n_sm), 256, 0, st>>>(
       nodes, n_elem, npe, ebox, d_bad, nullptr);
-  unsigned gf = (unsigned)((n_faces + TB - 1) / TB);
+  unsigned gf = (unsigned)((n_faces * TAG_R + TB - 1) / TB);
   k_surface<<<dim3((unsigned)((n_faces + SURF_FPB - 1) / SURF_FPB), 1), TB, 0, st>>>(d_inst);
   k_clear<<<dim3(64, 1), TB, 0, st>>>(d_inst);
   k_tag<<<gf, TB, 0, st>>>(d_inst, d_off, 1, n_faces);

@@ -18,6 +18,7 @@
 #pragma once
 
 #include "dc_common.cuh"
+#include "dc_frames.cuh"
 
 namespace dc {
 
@@ -27,19 +28,26 @@ __constant__ unsigned char c_ftri[MAX_Q][MAX_NTF][3];   // cut-face triangles, p
 constexpr int CUBE_PITCH = 96;  // bytes per x-row of the hole map (>= MAX_DIM, 16-byte multiple)
 
 // ------------------------------------------------------------------ a1 + a2
-constexpr int SURF_FPB = 32;  // faces per block of k_surface
+constexpr int SURF_FPB = 16;  // faces per block of k_surface (a tile of the fused prep kernel)
 
-// hole-map and bin geometry of one instance from its surface box
+// hole-map and bin geometry of one instance from its surface box.  Any cube
+// size serves (every consumer rounds outward and reads the one stored value),
+// so it is derived in FP32, where this GPU's FP64 pipe would take
+// microseconds of one thread's time: ds is a float (exact in FP64), the cube
+// counts cover the box with a padding cube on each side (an underestimate of
+// one cube from rounding is within that padding).
 __device__ void grid_from_box(Inst& in) {
-  double lo[3], hi[3], L = 0.0;
+  double lo[3], hi[3];
+  float span[3], L = 0.f;
   for (int a = 0; a < 3; ++a) {
     lo[a] = dkey_decode(atomicOr(&in.sbox_key[a], 0ull));
     hi[a] = dkey_decode(atomicOr(&in.sbox_key[3 + a], 0ull));
-    L = fmax(L, hi[a] - lo[a]);
+    span[a] = __double2float_ru(hi[a] - lo[a]);
+    L = fmaxf(L, span[a]);
   }
-  if (!(L > 0.0) || !(L < 1e300)) {
+  if (!(L > 0.f) || !(L < 1e30f)) {
     atomicOr(&in.err, (int)ERR_DEGENERATE);
-    L = 1.0;
+    L = 1.f;
   }
   // cubes on the longest side: as configured, or cubes_per_edge (1.8 unless
   // tuned) per element edge (a map much finer than the elements only
@@ -47,16 +55,17 @@ __device__ void grid_from_box(Inst& in) {
   // the band of candidates)
   int cells = in.holemap_cells;
   if (cells <= 0) {
-    const double a = in.h_elem > 0.f ? (double)in.cubes_per_edge * L / (double)in.h_elem : 64.0;
-    cells = (int)fmin(fmax(a + 0.5, 16.0), (double)MAX_CELLS);
+    const float a = in.h_elem > 0.f ? in.cubes_per_edge * L / in.h_elem : 64.f;
+    cells = (int)fminf(fmaxf(a + 0.5f, 16.f), (float)MAX_CELLS);
   }
-  const double ds = L / cells;
+  const float ds_f = L / (float)cells;
+  const float inv_ds = 1.0f / ds_f;
+  const double ds = (double)ds_f;
   in.ds = ds;
   int nb = 1;
   for (int a = 0; a < 3; ++a) {
-    double span = fmax(hi[a] - lo[a], 0.0) / ds;
-    int n = (int)ceil(fmin(span, (double)cells));
-    n = clampi(n, 1, cells);
+    const float cf = fminf(fmaxf(span[a], 0.f) * inv_ds, (float)cells);
+    const int n = clampi((int)ceilf(cf), 1, cells);
     in.dims[a] = n + 2;
     in.origin[a] = lo[a] - ds;
     in.bdims[a] = (in.dims[a] + in.bin_cubes - 1) / in.bin_cubes;
@@ -64,8 +73,8 @@ __device__ void grid_from_box(Inst& in) {
   }
   in.bs = ds * in.bin_cubes;
   for (int a = 0; a < 3; ++a) in.origin_f[a] = (float)in.origin[a];
-  in.inv_ds_f = (float)(1.0 / ds);
-  in.inv_bs_f = (float)(1.0 / in.bs);
+  in.inv_ds_f = inv_ds;
+  in.inv_bs_f = 1.0f / (ds_f * (float)in.bin_cubes);
   if (nb > in.nbins_cap) atomicOr(&in.err, (int)ERR_DEGENERATE);  // sized on the host for the worst case
 }
 
@@ -91,6 +100,15 @@ __device__ void surface_tile(Inst& in, long long f0, bool derive_grid) {
   if (threadIdx.x < 3) s_ext[threadIdx.x] = 0u;
   const double* src = in.faces_in + f0 * npf * 3;
   double* dst = in.surf + f0 * npf * 3;
+  // |v| >= 1e300 or not finite, tested on the bit pattern (32-bit words: the
+  // FP64 pipe of this GPU is slow)
+  const int bigh = (int)(__double_as_longlong(1e300) >> 32);
+  const unsigned bigl = (unsigned)__double_as_longlong(1e300);
+  auto huge = [&](double v) {
+    const long long b = __double_as_longlong(v);
+    const int mh = (int)(b >> 32) & 0x7fffffff;
+    return mh > bigh || (mh == bigh && (unsigned)b >= bigl);
+  };
   bool bad = false;
   if (in.has_pose) {
     for (int k = threadIdx.x; k < nf * npf; k += blockDim.x) {
@@ -101,7 +119,7 @@ __device__ void surface_tile(Inst& in, long long f0, bool derive_grid) {
         const double v = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[0], x), __dmul_rn(R[1], y)), __dmul_rn(R[2], z)), R[3]);
         s_x[3 * k + a] = v;
         dst[3 * k + a] = v;
-        bad |= !(fabs(v) < 1e300);
+        bad |= huge(v);
       }
     }
   } else {
@@ -109,19 +127,21 @@ __device__ void surface_tile(Inst& in, long long f0, bool derive_grid) {
       const double v = src[k];
       s_x[k] = v;
       dst[k] = v;
-      bad |= !(fabs(v) < 1e300);
+      bad |= huge(v);
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&in.err, (int)ERR_NONFINITE);
-  // face boxes: thread (face, axis)
+  // face boxes: thread (face, axis), on the order-preserving integer keys of
+  // the coordinates (all finite here, or the cut is rejected)
   if (threadIdx.x < nf * 3) {
     const int lf = threadIdx.x / 3, a = threadIdx.x - lf * 3;
-    double lo = INFINITY, hi = -INFINITY;
+    FbKey klo{INT_MAX, 0xffffffffu}, khi{INT_MIN, 0u};
     for (int k = 0; k < npf; ++k) {
-      const double v = s_x[(lf * npf + k) * 3 + a];
-      lo = fmin(lo, v);
-      hi = fmax(hi, v);
+      const FbKey q = fb_key(__double_as_longlong(s_x[(lf * npf + k) * 3 + a]));
+      if (fb_less(q, klo)) klo = q;
+      if (fb_less(khi, q)) khi = q;
     }
+    const double lo = fb_value(klo), hi = fb_value(khi);
     const long long f = f0 + lf;
     in.fbox[6 * f + a] = __double2float_rd(lo);
     in.fbox[6 * f + 3 + a] = __double2float_ru(hi);
@@ -179,6 +199,15 @@ __device__ void clear_inst(Inst& in, long long t, long long nt) {
   for (long long k = t; k < nrows; k += nt) in.row_cnt[k] = 0;
 }
 
+// the same over the map's, bins' and rows' full capacity (the grid not yet known)
+__device__ void clear_inst_cap(Inst& in, long long t, long long nt) {
+  uint4* c4 = reinterpret_cast<uint4*>(in.cube);
+  const long long n4 = (long long)MAX_DIM * MAX_DIM * CUBE_PITCH / 16;
+  for (long long k = t; k < n4; k += nt) c4[k] = make_uint4(0, 0, 0, 0);
+  for (long long k = t; k < in.nbins_cap; k += nt) in.bin_cnt[k] = 0;
+  for (long long k = t; k < (long long)MAX_DIM * MAX_DIM; k += nt) in.row_cnt[k] = 0;
+}
+
 __global__ void k_clear(Inst* __restrict__ I) {
   pdl_enter();
   clear_inst(I[blockIdx.y], (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
@@ -198,14 +227,21 @@ __device__ __forceinline__ int cube_floorf(float x, int n) {
   return (int)floorf(x);
 }
 
-// a3: NEAR tags of the hole map, and face -> bin (bin of the box's min corner)
+// a3: NEAR tags of the hole map, and face -> bin (bin of the box's min
+// corner).  TAG_R threads share a face: thread r tags the face's cube rows r,
+// r + TAG_R, ... (a face box spans a few rows of a few cubes each), and thread
+// 0 also files the face in its bin.  g numbers (face, r) pairs over all
+// instances.
+constexpr int TAG_R = 8;
 __device__ void tag_face(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total,
                          long long g) {
-  if (g >= nf_total) return;
-  int ii = find_inst(foff, n_inst, g);
+  const long long gf = g / TAG_R;
+  const int r = (int)(g - gf * TAG_R);
+  if (gf >= nf_total) return;
+  int ii = find_inst(foff, n_inst, gf);
   Inst& in = I[ii];
   if (in.err & ERR_DEGENERATE) return;
-  long long f = g - foff[ii];
+  long long f = gf - foff[ii];
   // cube range of the face box inflated by the fringe margin 2 tol, in float:
   // the extra 1e-3 cube (plus 16 ulp of the coordinates) only ever adds cubes
   const float mu = (float)(2.0 * in.tol);
@@ -215,87 +251,92 @@ __device__ void tag_face(Inst* __restrict__ I, const long long* __restrict__ fof
     float o = in.origin_f[a];
     float slack = 1e-3f + 16.0f * 5.9604645e-8f * (fabsf(lo) + fabsf(hi) + fabsf(o)) * in.inv_ds_f;
     float x0 = (lo - mu - o) * in.inv_ds_f - slack, x1 = (hi + mu - o) * in.inv_ds_f + slack;
-    c0[a] = max(cube_floor((double)x0, in.dims[a]), 0);
-    c1[a] = min(cube_floor((double)x1, in.dims[a]), in.dims[a] - 1);
-    b[a] = clampi(cube_floor((double)((lo - o) * in.inv_bs_f), in.bdims[a]), 0, in.bdims[a] - 1);
+    c0[a] = max(cube_floorf(x0, in.dims[a]), 0);
+    c1[a] = min(cube_floorf(x1, in.dims[a]), in.dims[a] - 1);
+    b[a] = clampi(cube_floorf((lo - o) * in.inv_bs_f, in.bdims[a]), 0, in.bdims[a] - 1);
   }
-  for (int z = c0[2]; z <= c1[2]; ++z)
-    for (int y = c0[1]; y <= c1[1]; ++y) {
+  const int ny = c1[1] - c0[1] + 1, nz = c1[2] - c0[2] + 1;
+  if (ny > 0 && nz > 0 && c1[0] >= c0[0])
+    for (int k = r; k < ny * nz; k += TAG_R) {
+      const int z = c0[2] + k / ny, y = c0[1] + k % ny;
       uint8_t* row = in.cube + ((long long)z * in.dims[1] + y) * CUBE_PITCH;
       for (int x = c0[0]; x <= c1[0]; ++x) row[x] = CUBE_NEAR;
     }
-  int bi = (b[2] * in.bdims[1] + b[1]) * in.bdims[0] + b[0];
-  in.fbin[f] = bi;
-  atomicAdd(&in.bin_cnt[bi], 1);
+  if (r == 0) {
+    int bi = (b[2] * in.bdims[1] + b[1]) * in.bdims[0] + b[0];
+    in.fbin[f] = bi;
+    atomicAdd(&in.bin_cnt[bi], 1);
+  }
 }
 
+// grid: nf_total * TAG_R threads
 __global__ void k_tag(Inst* __restrict__ I, const long long* __restrict__ foff, int n_inst, long long nf_total) {
   pdl_enter();
   tag_face(I, foff, n_inst, nf_total, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// exclusive scan of the bin counts (one CTA of 1024 threads per instance):
-// thread t takes the t-th chunk of consecutive bins (held in registers when a
-// chunk has at most BIN_PER_T bins, else read twice), the CTA scans the chunk
-// totals with warp shuffles; counts become cursors
-constexpr int BIN_PER_T = 10;
+// exclusive scan of the bin counts (one block per instance; 256 threads in
+// the fused prep kernel, 1024 in k_bin_scan), in passes of BIN_PER_T x 32
+// bins per warp: lane l of warp w holds bins base + 32 j + l (j < BIN_PER_T,
+// so every load and store of a warp is one contiguous span), the warp scans
+// each row of 32 with shuffles, the block scans the warp totals, and a carry
+// runs over the passes; counts become cursors (zero) as their offsets are
+// written
+constexpr int BIN_PER_T = 16;
 __device__ void bin_scan_inst(Inst& in) {
   __shared__ int wsum[32];
   const int nb = in.bdims[0] * in.bdims[1] * in.bdims[2];
   if ((in.err & ERR_DEGENERATE) || nb > in.nbins_cap) return;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, T = blockDim.x;
-  const int chunk = (nb + T - 1) / T;
-  const int b0 = min(t * chunk, nb), b1 = min(b0 + chunk, nb);
-  int c[BIN_PER_T];
-  int s = 0;
-  if (chunk <= BIN_PER_T) {
+  const unsigned FULL = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const int per_warp = 32 * BIN_PER_T;
+  int carry = 0;
+  for (int base = 0; base < nb; base += nw * per_warp) {
+    const int wb = base + wid * per_warp;
+    int v[BIN_PER_T];
 #pragma unroll
-    for (int k = 0; k < BIN_PER_T; ++k) {
-      c[k] = b0 + k < b1 ? in.bin_cnt[b0 + k] : 0;
-      s += c[k];
+    for (int j = 0; j < BIN_PER_T; ++j) {
+      const int idx = wb + 32 * j + lane;
+      v[j] = idx < nb ? in.bin_cnt[idx] : 0;
     }
-  } else {
-    for (int k = b0; k < b1; ++k) s += in.bin_cnt[k];
-  }
-  // inclusive scan of the chunk totals: within the warp, then over warps
-  int x = s;
+    int wrun = 0;  // the warp's running total before row j
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= d) x += v;
-  }
-  if (lane == 31) wsum[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int y = lane < (T >> 5) ? wsum[lane] : 0;
+    for (int j = 0; j < BIN_PER_T; ++j) {
+      int x = v[j];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, y, d);
-      if (lane >= d) y += v;
-    }
-    wsum[lane] = y;
-  }
-  __syncthreads();
-  int run = x - s + (wid > 0 ? wsum[wid - 1] : 0);
-  if (chunk <= BIN_PER_T) {
-#pragma unroll
-    for (int k = 0; k < BIN_PER_T; ++k) {
-      if (b0 + k < b1) {
-        in.bin_off[b0 + k] = run;
-        in.bin_cnt[b0 + k] = 0;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
       }
-      run += c[k];
+      const int row_total = __shfl_sync(FULL, x, 31);
+      v[j] = wrun + x - v[j];  // exclusive offset within the warp's span
+      wrun += row_total;
     }
-  } else {
-    for (int k = b0; k < b1; ++k) {
-      const int v = in.bin_cnt[k];
-      in.bin_off[k] = run;
-      in.bin_cnt[k] = 0;
-      run += v;
+    if (lane == 0) wsum[wid] = wrun;
+    __syncthreads();
+    if (wid == 0) {
+      int y = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int z = __shfl_up_sync(FULL, y, d);
+        if (lane >= d) y += z;
+      }
+      wsum[lane] = y;  // inclusive over warps
     }
+    __syncthreads();
+    const int off = carry + (wid > 0 ? wsum[wid - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < BIN_PER_T; ++j) {
+      const int idx = wb + 32 * j + lane;
+      if (idx < nb) {
+        in.bin_off[idx] = off + v[j];
+        in.bin_cnt[idx] = 0;
+      }
+    }
+    carry += wsum[nw - 1];
+    __syncthreads();  // wsum is rewritten by the next pass (or instance)
   }
-  if (t == T - 1) in.bin_off[nb] = wsum[(T >> 5) - 1];
-  __syncthreads();  // wsum may be reused by the next instance
+  if (t == 0) in.bin_off[nb] = carry;
 }
 
 __global__ void __launch_bounds__(1024) k_bin_scan(Inst* __restrict__ I) {
@@ -684,9 +725,10 @@ __device__ bool prep_barrier(unsigned* count, unsigned k, unsigned* timed_out) {
 }
 
 // The surface ingest, hole map, face bins and element classification of a
-// cut (a1-a4) in one cooperative launch: the seven steps are each a
-// grid-stride loop over their work, separated by grid barriers, which leaves
-// the launch and drain of seven small kernels out of the chain.  sync[0]
+// cut (a1-a4) in one cooperative launch: four steps (five for a batch), each
+// a grid-stride loop over independent pieces of work, separated by grid
+// barriers, which leaves the launch and drain of small kernels out of the
+// chain.  sync[0]
 // counts barrier arrivals, sync[1] records a barrier that ran out (the cut
 // then reports an internal error).
 // classify = 0: the classification is left to a separate k_classify launch
@@ -707,37 +749,74 @@ __global__ void __launch_bounds__(256) k_prep(Inst* __restrict__ I, const long l
   const long long gwarp = tid >> 5, nwarp = nthr >> 5;
   unsigned k = 0;
   // a1 + a2: pose and face boxes, SURF_FPB faces per block and step, the
-  // tiles of every instance spread over the whole grid
+  // tiles of every instance spread over the whole grid; the block that
+  // finishes an instance's last tile derives its hole-map grid (a tile
+  // counter per instance).  A single instance's map, bin counts and row
+  // counts are cleared here to their full capacity (under a megabyte), which
+  // needs no grid
+  if (n_inst == 1) {
+    clear_inst_cap(I[0], tid, nthr);
+    // the classification reads every element box last: start bringing them
+    // into L2 now (a hint, for grids whose boxes take a fraction of L2)
+    const long long bytes = I[0].n_elem * 24;
+    if (bytes <= (32ll << 20)) {
+      const char* eb = reinterpret_cast<const char*>(I[0].eaabb);
+      for (long long o = tid * 128; o < bytes; o += nthr * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(eb + o));
+    }
+  }
   for (long long t = blockIdx.x; t < toff[n_inst]; t += gridDim.x) {
     const int ii = find_inst(toff, n_inst, t);
-    surface_tile(I[ii], (t - toff[ii]) * SURF_FPB, false);
+    surface_tile(I[ii], (t - toff[ii]) * SURF_FPB, true);
   }
   if (!prep_barrier(sync, ++k, sync + 1)) return;
-  for (long long ii = tid; ii < n_inst; ii += nthr) grid_from_box(I[ii]);
+  if (n_inst > 1) {
+    // a batch clears what its grids use
+    for (int ii = 0; ii < n_inst; ++ii) clear_inst(I[ii], tid, nthr);
+    if (!prep_barrier(sync, ++k, sync + 1)) return;
+  }
+  // a3: NEAR cubes tagged and bins counted; the row centre lines' crossings
+  // (which read only the posed surface and the grid) alongside
+  // (one index space, so that the two kinds of work run on different threads)
+  {
+    const long long ntag = nf_total * TAG_R, nall = ntag + troff[n_inst];
+    for (long long g = tid; g < nall; g += nthr) {
+      if (g < ntag) {
+        tag_face(I, foff, n_inst, nf_total, g);
+      } else {
+        const long long gt = g - ntag;
+        const int ii = find_inst(troff, n_inst, gt);
+        row_cross(I[ii], gt - troff[ii]);
+      }
+    }
+  }
   if (!prep_barrier(sync, ++k, sync + 1)) return;
-  // a3: clear the map and counters, then tag NEAR cubes and count bins
-  for (int ii = 0; ii < n_inst; ++ii) clear_inst(I[ii], tid, nthr);
+  // the bin counts scanned (a block per instance) while the other blocks
+  // label the rows (crossings and NEAR tags are complete)
+  {
+    const int n_scan = min(n_inst, (int)(gridDim.x / 2));
+    if ((int)blockIdx.x < n_scan) {
+      for (int ii = blockIdx.x; ii < n_inst; ii += n_scan) bin_scan_inst(I[ii]);
+    } else {
+      const long long wpb = blockDim.x >> 5;
+      const long long lw = gwarp - (long long)n_scan * wpb, nlw = nwarp - (long long)n_scan * wpb;
+      for (int ii = 0; ii < n_inst; ++ii) {
+        Inst& in = I[ii];
+        const long long nrows = (long long)in.dims[1] * in.dims[2];
+        for (long long r = lw; r < nrows; r += nlw) row_label(in, (int)r, lane);
+      }
+    }
+  }
   if (!prep_barrier(sync, ++k, sync + 1)) return;
-  for (long long g = tid; g < nf_total; g += nthr) tag_face(I, foff, n_inst, nf_total, g);
-  if (!prep_barrier(sync, ++k, sync + 1)) return;
-  for (int ii = blockIdx.x; ii < n_inst; ii += gridDim.x) bin_scan_inst(I[ii]);
-  if (!prep_barrier(sync, ++k, sync + 1)) return;
-  // faces into their bins, and the row centre lines' crossings
+  // a4: faces into their bins, and every element against the map (warps
+  // step together for the compaction), on separate threads
+  // (the classification's index space starts after the fill's threads,
+  // rounded to whole blocks so that warps stay aligned)
+  const long long nfill = (nf_total + 255) / 256 * 256;
   for (long long g = tid; g < nf_total; g += nthr) bin_fill(I, foff, n_inst, nf_total, g);
-  for (long long g = tid; g < troff[n_inst]; g += nthr) {
-    const int ii = find_inst(troff, n_inst, g);
-    row_cross(I[ii], g - troff[ii]);
-  }
-  if (!prep_barrier(sync, ++k, sync + 1)) return;
-  for (int ii = 0; ii < n_inst; ++ii) {
-    Inst& in = I[ii];
-    const long long nrows = (long long)in.dims[1] * in.dims[2];
-    for (long long r = gwarp; r < nrows; r += nwarp) row_label(in, (int)r, lane);
-  }
   if (!classify) return;
-  if (!prep_barrier(sync, ++k, sync + 1)) return;
-  // a4: every element against the map (warps step together for the compaction)
-  for (long long base = tid - lane; base < ne_total; base += nthr) classify_elem(I, eoff, n_inst, ne_total, cl, cnt, base + lane);
+  const long long first = nfill < nthr / 2 ? nfill : 0;
+  for (long long base = tid - lane - first; base < ne_total; base += nthr)
+    if (base >= 0) classify_elem(I, eoff, n_inst, ne_total, cl, cnt, base + lane);
 }
 
 }  // namespace dc

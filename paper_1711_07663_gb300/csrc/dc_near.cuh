@@ -77,44 +77,45 @@ __device__ __forceinline__ bool near_separated(const V3<float>* A, const V3<floa
   return sa || sb;
 }
 
-// The crossing tests of the triangle-triangle test without divisions: an
-// edge PQ whose end points lie strictly on opposite sides of the other
-// triangle's plane crosses it when the three signed volumes of PQ with the
-// triangle's edges share a strict sign.  The first such edge (in the test's
-// order) is certified for the exact triangles.  True if the pair certainly
-// crosses (its element is fringe).
-__device__ __forceinline__ bool edge_through(V3<float> P, V3<float> Q, const V3<float>* t) {
+// Certified crossings without divisions.  A signed volume of four of the
+// float points, evaluated as in orient_cert, moves by at most
+// B = 8 rho L^2 + 16 rho^2 L + 32 u L^3 when the points move to the exact
+// (FP64) ones within rho = 2 u S, for L at least the longest edge vector plus
+// 2 rho (orient_cert's bound).  Every point lies in [-S, S]^3, so
+// L = 2 sqrt(3) S (1 + 1e-4) + 2 rho serves for all of them: one bound per
+// pair instead of one square root per volume, never below orient_cert's.
+// An edge PQ of one triangle crosses the other when P and Q lie beyond B on
+// opposite sides of its plane and the three volumes of PQ with its edges
+// exceed B in one sign; then the exact triangles intersect.  True if some
+// edge of either triangle certainly crosses the other (the element is
+// fringe).
+__device__ __forceinline__ bool edge_cert(V3<float> P, V3<float> Q, const V3<float>* t, float B) {
   const V3<float> d = Q - P, e0 = t[0] - P, e1 = t[1] - P, e2 = t[2] - P;
   const float o0 = dot(cross(d, e0), e1), o1 = dot(cross(d, e1), e2), o2 = dot(cross(d, e2), e0);
-  return (o0 > 0.f && o1 > 0.f && o2 > 0.f) || (o0 < 0.f && o1 < 0.f && o2 < 0.f);
+  return (o0 > B && o1 > B && o2 > B) || (o0 < -B && o1 < -B && o2 < -B);
 }
 __device__ __forceinline__ bool near_cross(const V3<float>* a, const V3<float>* b, float S) {
-  const float rho = 2.0f * Eps<float>::u * S;
+  const float u = Eps<float>::u;
+  const float rho = 2.0f * u * S;
+  const float L = 3.4646f * S + 2.0f * rho;
+  // (1.01: the rounding of the bound's own evaluation)
+  const float B = 1.01f * (8.0f * rho * L * L + 16.0f * rho * rho * L + 32.0f * u * L * L * L);
   const V3<float> na = cross(a[1] - a[0], a[2] - a[0]), nb = cross(b[1] - b[0], b[2] - b[0]);
   float sb[3], sa[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) { sb[j] = dot(na, b[j] - a[0]); sa[j] = dot(nb, a[j] - b[0]); }
-  int xc = -1;
+  bool hit = false;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const int k = (j + 1) % 3;
-    if (xc < 0 && ((sb[j] > 0.f && sb[k] < 0.f) || (sb[j] < 0.f && sb[k] > 0.f)) && edge_through(b[j], b[k], a)) xc = j;
+    if (!hit && ((sb[j] > B && sb[k] < -B) || (sb[j] < -B && sb[k] > B))) hit = edge_cert(b[j], b[k], a, B);
   }
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const int k = (j + 1) % 3;
-    if (xc < 0 && ((sa[j] > 0.f && sa[k] < 0.f) || (sa[j] < 0.f && sa[k] > 0.f)) && edge_through(a[j], a[k], b))
-      xc = 3 + j;
+    if (!hit && ((sa[j] > B && sa[k] < -B) || (sa[j] < -B && sa[k] > B))) hit = edge_cert(a[j], a[k], b, B);
   }
-  if (__any_sync(__activemask(), xc >= 0)) {
-    // one uniform call: lanes without a crossing certify a dummy and ignore it
-    const int j = xc < 0 ? 0 : xc % 3;
-    const V3<float>* se = (xc < 3) ? b : a;
-    const V3<float>* tt = (xc < 3) ? a : b;
-    const bool cert = certified_cross<float>(pick3(se, j), pick3(se, (j + 1) % 3), tt[0], tt[1], tt[2], rho);
-    return xc >= 0 && cert;
-  }
-  return false;
+  return hit;
 }
 
 // FP64 distance of one triangle pair, the 21 parts of the triangle-triangle

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
   const int bigh = (int)(__double_as_longlong(1e300) >> 32);
   const unsigned bigl = (unsigned)__double_as_longlong(1e300);
   const long long stride = (long long)gridDim.x * (blockDim.x / FB_GROUP);
-  double ext_acc = 0.0;
+  float ext_acc = 0.f;  // this thread's share of the extent sum
   bool nonfinite = false;
   // the loop runs in step across each warp (its groups' shuffles)
   for (long long e0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / FB_GROUP; e0 < n_elem;
@@ -339,22 +339,26 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
         if (fb_less(ol, lo[a])) lo[a] = ol;
         if (fb_less(hi[a], oh)) hi[a] = oh;
       }
-    if (valid && r == 0) {
-      double ext = 0.0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double dl = fb_value(lo[a]), dh = fb_value(hi[a]);
-        box[6 * e + a] = __double2float_rd(dl);
-        box[6 * e + 3 + a] = __double2float_ru(dh);
-        ext = fmax(ext, dh - dl);
-      }
-      if (ext < 1e300) ext_acc += ext;
+    // thread r < 3 of the group rounds axis r outward (one FP64 conversion
+    // pair per thread instead of three on one: this GPU's FP64 pipe is slow);
+    // the element's extent, which only sizes the hole map, is taken in float
+    float ext = 0.f;
+    if (valid && r < 3) {
+      const FbKey kl = r == 0 ? lo[0] : (r == 1 ? lo[1] : lo[2]);
+      const FbKey kh = r == 0 ? hi[0] : (r == 1 ? hi[1] : hi[2]);
+      const float bl = __double2float_rd(fb_value(kl)), bh = __double2float_ru(fb_value(kh));
+      box[6 * e + r] = bl;
+      box[6 * e + 3 + r] = bh;
+      ext = bh - bl;
     }
+    ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, 1));
+    ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, 2));
+    if (valid && r == 0 && ext < 1e30f) ext_acc += ext;
   }
   if (__any_sync(0xffffffffu, nonfinite) && lane == 0) atomicOr(bad, 1);
   if (ext_sum) {
     for (int s = 16; s; s >>= 1) ext_acc += __shfl_xor_sync(0xffffffffu, ext_acc, s);
-    if (lane == 0 && ext_acc > 0.0) atomicAdd(ext_sum, ext_acc);
+    if (lane == 0 && ext_acc > 0.f) atomicAdd(ext_sum, (double)ext_acc);
   }
 }
 

@@ -269,6 +269,29 @@ def cpu_oracle_sample(case, seconds, seed=0, threads=0):
     return done, dt, ncpu
 
 
+def config1_oracle(n_sample=512, seed=7):
+    """The oracle's two modes on the 16^3 Q2 plain workload (4096 elements, 384
+    Q2 faces): branch and bound on the whole grid, and brute force (every
+    triangle pair of every element-face pair) on a seeded sample of elements,
+    scaled to the grid; both on all host threads, flags compared on the
+    sample."""
+    import oracle as O
+    case = _plain16()
+    t0 = time.perf_counter()
+    flags, _, _, st = O.cut(case.p, case.nodes, case.q, case.faces)
+    t_pruned = time.perf_counter() - t0
+    ids = np.sort(np.random.default_rng(seed).choice(case.n_elem, size=n_sample, replace=False))
+    t0 = time.perf_counter()
+    fb, _, _, sb = O.cut(case.p, case.nodes, case.q, case.faces, ids=ids, brute=True)
+    t_brute = time.perf_counter() - t0
+    return {"workload": "16^3 Q2 hexes cut by a sphere of 384 Q2 faces (4096 elements)",
+            "pruned_ms_per_cut": t_pruned * 1e3, "pruned_tritri_tests": int(st["tritri_tests"]),
+            "brute_ms_per_cut": t_brute * case.n_elem / n_sample * 1e3,
+            "brute_tritri_tests_per_s": sb["tritri_tests"] / t_brute,
+            "brute_sample": f"{n_sample} seeded elements ({t_brute:.1f} s), scaled to all {case.n_elem}",
+            "brute_same_flags": bool(np.array_equal(fb, flags[ids])), "threads": os.cpu_count()}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -858,7 +881,8 @@ def run_ours(args, world, rank, local):
         cpu = {"value": S_STAR * done / NE / dt, "unit": UNIT, "cores": ncpu, "kind": "oracle",
                "sample": f"{done} random elements of the workload ({dt:.1f} s, all {ncpu} host threads); "
                          f"one cut = the sampled time scaled to all {NE} elements",
-               "single_thread_value": S_STAR * d1 / NE / t1, "cpu_model": cpu_model()}
+               "single_thread_value": S_STAR * d1 / NE / t1, "cpu_model": cpu_model(),
+               "config1": config1_oracle()}
 
     if rank == 0:
         line = {

@@ -247,8 +247,10 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
 // covers 32 contiguous bytes of each of its 8 elements), twelve at a time, so
 // that within each twelve its three values fall on the axes r mod 3, r + 1 and
 // r + 2 mod 3 in that order: fixed accumulators, no indexing by axis.  The
-// boxes are taken on integer keys of the FP64 bit patterns, compared as pairs
-// of 32-bit words.
+// boxes are taken on order-preserving 64-bit integer keys of the FP64 bits
+// (fr_key), so the sweep does no FP64 arithmetic but the final outward
+// rounding; a coordinate of magnitude 1e300 or more, or not finite, is found
+// on the reduced keys.
 // No shared memory or barrier: the whole SM's warps keep loads in flight,
 // which is what the sweep (a pure stream over the node array) needs.  The
 // grid is one wave (fb_grid): the loop strides over the elements, so no SM
@@ -256,8 +258,8 @@ __global__ void __launch_bounds__(FR_THREADS) k_elem_frames(const double* __rest
 constexpr int FB_GROUP = 4;
 
 // an order-preserving key of a finite double as two 32-bit words (high word
-// signed, low word unsigned, compared in that order): 64-bit integer compares
-// would run on GB300's slow FP64 pipe, 32-bit ones run on the integer pipe
+// signed, low word unsigned, compared in that order; the surface tiles' face
+// boxes use it)
 struct FbKey {
   int h;
   unsigned l;
@@ -280,12 +282,9 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
                                                     float* __restrict__ box, int* __restrict__ bad,
                                                     double* __restrict__ ext_sum) {
   const int lane = threadIdx.x & 31, r = lane & (FB_GROUP - 1);
-  // in-element indices are 32-bit: GB300 runs 64-bit integer compares on its
-  // slow FP64 pipe
-  const int nval = 3 * npe;
-  // |x| >= 1e300 (or not finite) on the high word, then the low word
-  const int bigh = (int)(__double_as_longlong(1e300) >> 32);
-  const unsigned bigl = (unsigned)__double_as_longlong(1e300);
+  const int nval = 3 * npe;  // in-element indices are 32-bit (measured faster)
+  // keys of +-1e300: a reduced box beyond them holds a huge or non-finite node
+  const long long kbig64 = fr_key(__double_as_longlong(1e300)), knbig64 = fr_key(__double_as_longlong(-1e300));
   const long long stride = (long long)gridDim.x * (blockDim.x / FB_GROUP);
   float ext_acc = 0.f;  // this thread's share of the extent sum
   bool nonfinite = false;
@@ -294,8 +293,7 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
        e0 += stride) {
     const long long e = e0 + (lane >> 2);
     const bool valid = e < n_elem;
-    const FbKey top{INT_MAX, 0xffffffffu}, bot{INT_MIN, 0u};
-    FbKey lo0 = top, lo1 = top, lo2 = top, hi0 = bot, hi1 = bot, hi2 = bot;
+    long long lo0 = LLONG_MAX, lo1 = LLONG_MAX, lo2 = LLONG_MAX, hi0 = LLONG_MIN, hi1 = LLONG_MIN, hi2 = LLONG_MIN;
     if (valid) {
       const long long* x = reinterpret_cast<const long long*>(nodes) + e * nval;
 #pragma unroll 4
@@ -307,23 +305,15 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
         const long long b1 = __ldg(x + (i1 < nval ? i1 : 0));
         const long long b2 = __ldg(x + (i2 < nval ? i2 : 0));
         const bool v0 = i0 < nval, v1 = i1 < nval, v2 = i2 < nval;
-        const long long bb[3] = {b0, b1, b2};
-        const bool vv[3] = {v0, v1, v2};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int mh = (int)(bb[j] >> 32) & 0x7fffffff;
-          const unsigned ml = (unsigned)bb[j];
-          nonfinite |= vv[j] && (mh > bigh || (mh == bigh && ml >= bigl));
-        }
-        const FbKey q0 = fb_key(b0), q1 = fb_key(b1), q2 = fb_key(b2);
-        if (v0) { if (fb_less(q0, lo0)) lo0 = q0; if (fb_less(hi0, q0)) hi0 = q0; }
-        if (v1) { if (fb_less(q1, lo1)) lo1 = q1; if (fb_less(hi1, q1)) hi1 = q1; }
-        if (v2) { if (fb_less(q2, lo2)) lo2 = q2; if (fb_less(hi2, q2)) hi2 = q2; }
+        const long long q0 = fr_key(b0), q1 = fr_key(b1), q2 = fr_key(b2);
+        if (v0) { lo0 = min(lo0, q0); hi0 = max(hi0, q0); }
+        if (v1) { lo1 = min(lo1, q1); hi1 = max(hi1, q1); }
+        if (v2) { lo2 = min(lo2, q2); hi2 = max(hi2, q2); }
       }
     }
     // accumulator j of thread r holds axis (r + j) mod 3: put them in axis order
     const int m = r % 3;
-    FbKey lo[3], hi[3];
+    long long lo[3], hi[3];
     lo[0] = m == 0 ? lo0 : (m == 1 ? lo2 : lo1);
     lo[1] = m == 0 ? lo1 : (m == 1 ? lo0 : lo2);
     lo[2] = m == 0 ? lo2 : (m == 1 ? lo1 : lo0);
@@ -334,19 +324,20 @@ __global__ void __launch_bounds__(256) k_elem_boxes(const double* __restrict__ n
     for (int s = 1; s < FB_GROUP; s <<= 1)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const FbKey ol{__shfl_xor_sync(0xffffffffu, lo[a].h, s), __shfl_xor_sync(0xffffffffu, lo[a].l, s)};
-        const FbKey oh{__shfl_xor_sync(0xffffffffu, hi[a].h, s), __shfl_xor_sync(0xffffffffu, hi[a].l, s)};
-        if (fb_less(ol, lo[a])) lo[a] = ol;
-        if (fb_less(hi[a], oh)) hi[a] = oh;
+        lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], s));
+        hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], s));
       }
     // thread r < 3 of the group rounds axis r outward (one FP64 conversion
     // pair per thread instead of three on one: this GPU's FP64 pipe is slow);
     // the element's extent, which only sizes the hole map, is taken in float
     float ext = 0.f;
     if (valid && r < 3) {
-      const FbKey kl = r == 0 ? lo[0] : (r == 1 ? lo[1] : lo[2]);
-      const FbKey kh = r == 0 ? hi[0] : (r == 1 ? hi[1] : hi[2]);
-      const float bl = __double2float_rd(fb_value(kl)), bh = __double2float_ru(fb_value(kh));
+      const long long kl = r == 0 ? lo[0] : (r == 1 ? lo[1] : lo[2]);
+      const long long kh = r == 0 ? hi[0] : (r == 1 ? hi[1] : hi[2]);
+      nonfinite |= kh >= kbig64 || kl <= knbig64;
+      // (the key map is its own inverse)
+      const float bl = __double2float_rd(__longlong_as_double(fr_key(kl)));
+      const float bh = __double2float_ru(__longlong_as_double(fr_key(kh)));
       box[6 * e + r] = bl;
       box[6 * e + 3 + r] = bh;
       ext = bh - bl;

@@ -57,9 +57,9 @@ FLOPS_PER_KEY = 83.0
 # Jacobian (27 x 32), the 1-D bases (72) and the 3x3 solve (60)
 FLOPS_PER_NEWTON_STEP_Q2 = 996.0
 # DRAM bytes (read + write) of one k_near_main launch at the scale workload,
-# from the ncu capture summarised in profiles/k_near_main_scale64.md; None
-# until the current kernel has been captured
-K_NEAR_MAIN_TRAFFIC = None
+# from the ncu capture summarised in profiles/k_near_main_scale64.md
+# (8.338432 MB read + 0.046592 MB written); None once the kernel changes
+K_NEAR_MAIN_TRAFFIC = 8_385_024
 # resident-mesh bytes one cut must move: a FP32 box read and a flag written per
 # element, the FP64 nodes of each element that needs the exact test (Q2: 27
 # nodes x 3 x 8 B; its frame is formed from them), the FP64 face nodes (Q2:
@@ -269,7 +269,7 @@ def cpu_oracle_sample(case, seconds, seed=0, threads=0):
     return done, dt, ncpu
 
 
-def config1_oracle(n_sample=512, seed=7):
+def config1_oracle(n_sample=256, seed=7):
     """The oracle's two modes on the 16^3 Q2 plain workload (4096 elements, 384
     Q2 faces): branch and bound on the whole grid, and brute force (every
     triangle pair of every element-face pair) on a seeded sample of elements,

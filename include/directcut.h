@@ -36,7 +36,7 @@
  *
  * Ownership: the caller owns every pointer it passes.  dc_create copies the
  * meshes to the device.  dc_cut reads the request's inputs before it returns.
- * dc_submit copies host face nodes and the pose into library-owned memory
+ * dc_submit uploads host face nodes to the device (and copies the pose)
  * before it returns, so the caller may overwrite them at once; device face
  * nodes are read by the cut on the GPU and must stay unchanged until dc_poll
  * reports completion.  Output buffers must stay valid until dc_cut returns, or
@@ -110,8 +110,8 @@ typedef struct {
     int32_t max_inflight;     /* serving slots for dc_submit, 1..64; 0 -> 4 */
     int32_t profile;          /* 1: time each phase with CUDA events (dc_get_stats) */
     int32_t reserve_faces;    /* dc_create sizes every slot's device arena and pinned
-                                 staging (instance records, counters, host flags, host
-                                 face nodes of dc_submit) for one request of this many
+                                 staging (instance records, counters, host flags) for
+                                 one request of this many
                                  order-2 faces on the largest mesh, from one device block
                                  and one pinned block, so such requests never allocate
                                  (larger ones, and the first dc_submit with host
@@ -190,9 +190,9 @@ dc_status dc_cut(dc_ctx *ctx, int32_t mesh, const dc_request *req);
 dc_status dc_cut_batch(dc_ctx *ctx, int32_t n, const int32_t *meshes, const dc_request *reqs);
 
 /* Serving: admit a request into a free slot (DC_EBUSY when none is free or the
- * memory budget is exhausted), copy its host inputs (face nodes into the
- * slot's pinned staging, the pose), enqueue the cut on the slot's stream and
- * return a ticket.  Requests in different slots overlap on the GPU.  A request
+ * memory budget is exhausted), take its host inputs (host face nodes are
+ * uploaded on the slot's stream and the call waits for that copy; the pose is
+ * copied), enqueue the cut on the slot's stream and return a ticket.  Requests in different slots overlap on the GPU.  A request
  * within the slot's reservation (dc_config.reserve_faces) allocates nothing. */
 dc_status dc_submit(dc_ctx *ctx, int32_t mesh, const dc_request *req, uint64_t *ticket);
 

@@ -239,12 +239,9 @@ struct Slot {
   double* h_dist = nullptr;
   size_t h_out_cap = 0;
   size_t h_dist_cap = 0;
-  // pinned copy of a submitted request's host face nodes: dc_submit copies
-  // them here before it returns, and the upload reads this copy, so the caller
-  // may reuse its buffer at once (a slot is reused only after its ticket is
-  // collected, so the copy is never overwritten while its upload is pending)
-  double* h_faces = nullptr;
-  size_t h_faces_cap = 0;         // doubles
+  // completion of a submitted request's upload of host face nodes: dc_submit
+  // waits on it before it returns, so the caller may reuse its buffer at once
+  cudaEvent_t in_done = nullptr;
   bool busy = false;
   uint64_t ticket = 0;
   // in-flight bookkeeping
@@ -508,19 +505,6 @@ dc_status ensure_host(dc_ctx* c, Slot& s, size_t n_inst, long long ne_total, boo
   return DC_OK;
 }
 
-// pinned staging for a submitted request's host face nodes (n doubles)
-dc_status ensure_face_stage(dc_ctx* c, Slot& s, size_t n) {
-  if (s.h_faces_cap >= n) return DC_OK;
-  host_free(c, s.h_faces);
-  s.h_faces = nullptr;
-  s.h_faces_cap = 0;
-  if (host_alloc(&s.h_faces, sizeof(double) * n) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(DC_ENOMEM, "cudaMallocHost(%zu) for the face staging failed", sizeof(double) * n);
-  }
-  s.h_faces_cap = n;
-  return DC_OK;
-}
 
 dc_status validate_req(dc_ctx* c, int mesh, const dc_request* r) {
   if (!r) return fail(DC_EINVAL, "request is NULL");
@@ -689,11 +673,12 @@ dc_status launch_graph(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t s
   return DC_OK;
 }
 
-// Enqueue the whole cut of a batch on slot s (no host synchronisation).
-// copy_inputs: the call returns before the cut has read its inputs (dc_submit),
-// so host face nodes are first copied into the slot's pinned staging; the
-// synchronous calls upload straight from the caller's buffer, which stays
-// valid until they return.
+// Enqueue the whole cut of a batch on slot s.  Host face nodes are uploaded
+// straight from the caller's buffer.  copy_inputs: the call returns before the
+// cut has run (dc_submit), so enqueue waits for those uploads before it
+// returns (on any return once they are queued) and the caller may reuse its
+// buffer at once; the synchronous calls need no wait, their caller's buffer
+// stays valid until they return.
 dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_t st, bool copy_inputs) {
   NvtxRange nr("directcut: enqueue");
   const int n = (int)v.size();
@@ -716,14 +701,13 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     for (auto& r : v) host_dist |= !r.req->on_device && r.req->dist_out != nullptr;
   rc = ensure_host(c, s, (size_t)n, ne_total, host_dist);
   if (rc) return rc;
-  size_t host_face_doubles = 0;
-  if (copy_inputs) {
-    for (auto& r : v)
-      if (!r.req->on_device) host_face_doubles += (size_t)r.req->n_faces * (r.req->q + 1) * (r.req->q + 1) * 3;
-    rc = ensure_face_stage(c, s, host_face_doubles);
-    if (rc) return rc;
-  }
-  size_t hf_off = 0;
+  bool uploaded = false;  // host face nodes queued for upload
+  struct UploadWait {
+    cudaEvent_t ev = nullptr;
+    ~UploadWait() {
+      if (ev) cudaEventSynchronize(ev);
+    }
+  } upload_wait;
   // carve the arena
   char* p = s.arena.base;
   auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return r; };
@@ -749,14 +733,9 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     } else {
       double* stage = (double*)take(sizeof(double) * F * npf * 3);
       const size_t nd = (size_t)F * npf * 3;
-      const double* src = r->face_nodes;
-      if (copy_inputs) {
-        memcpy(s.h_faces + hf_off, r->face_nodes, sizeof(double) * nd);
-        src = s.h_faces + hf_off;
-        hf_off += nd;
-      }
-      CK(cudaMemcpyAsync(stage, src, sizeof(double) * nd, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(stage, r->face_nodes, sizeof(double) * nd, cudaMemcpyHostToDevice, st));
       in.faces_in = stage;
+      uploaded = true;
     }
     in.has_pose = r->pose ? 1 : 0;
     if (r->pose) memcpy(in.pose, r->pose, sizeof(double) * 12);
@@ -821,6 +800,10 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
     off += in.n_elem;
   }
 
+  if (copy_inputs && uploaded) {
+    CK(cudaEventRecord(s.in_done, st));
+    upload_wait.ev = s.in_done;
+  }
   CK(cudaMemcpyAsync(d_inst, s.h_inst, sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_off, s.h_off, sizeof(long long) * NOFF * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(s.ring_ev[s.cur_ring], st));
@@ -851,7 +834,7 @@ dc_status enqueue(dc_ctx* c, Slot& s, const std::vector<InstReq>& v, cudaStream_
   s.d_inst = d_inst;
   s.d_cnt = d_cnt;
   s.near = lp.near;
-  return DC_OK;
+  return DC_OK;  // (a submitted request's upload is waited for on the way out)
 }
 
 // copy results of a finished (synchronised) batch back and turn device error
@@ -921,6 +904,7 @@ dc_status init_slot(Slot& s, int prof) {
   CK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
   for (int r = 0; r < Slot::RING; ++r) CK(cudaEventCreateWithFlags(&s.ring_ev[r], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming));
   if (prof)
     for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&s.ev[i]));
   return DC_OK;
@@ -939,7 +923,7 @@ void free_slot(dc_ctx* c, Slot& s) {
   host_free(c, s.h_cnt);
   host_free(c, s.h_flags);
   host_free(c, s.h_dist);
-  host_free(c, s.h_faces);
+  if (s.in_done) cudaEventDestroy(s.in_done);
   for (int i = 0; i < 6; ++i)
     if (s.ev[i]) cudaEventDestroy(s.ev[i]);
   if (s.done) cudaEventDestroy(s.done);
@@ -1114,18 +1098,11 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
     for (auto& m : c->meshes) ne_max = std::max(ne_max, m.n_elem);
     const std::vector<SurfNeed> one{{(long long)cfg.reserve_faces, RESERVE_Q, true}};
     const size_t need = al256(arena_bytes(c, one, ne_max));
-    const size_t stage = (size_t)cfg.reserve_faces * (RESERVE_Q + 1) * (RESERVE_Q + 1) * 3;
     const size_t n_slots = c->slots.size();
-    auto serving = [&](size_t i) { return i > 0 || n_slots == 1; };
-    // host staging of one slot: instance ring, counters, outputs, and the
-    // face copy of a submitted request (serving slots)
+    // host staging of one slot: instance ring, counters, host flags
     const size_t ring_one = al256(sizeof(Inst)) + al256(sizeof(long long) * NOFF * 2);
-    auto host_need = [&](size_t i) {
-      return Slot::RING * ring_one + al256(sizeof(unsigned long long) * NCNT) + al256((size_t)ne_max) +
-             (serving(i) ? al256(sizeof(double) * stage) : 0);
-    };
-    size_t host_total = 0;
-    for (size_t i = 0; i < n_slots; ++i) host_total += host_need(i);
+    const size_t host_one = Slot::RING * ring_one + al256(sizeof(unsigned long long) * NCNT) + al256((size_t)ne_max);
+    const size_t host_total = host_one * n_slots;
     if (!cfg.mem_budget_bytes || c->mesh_bytes + need * n_slots <= cfg.mem_budget_bytes) {
       if (dev_alloc(&c->dev_block, need * n_slots) != cudaSuccess) {
         cudaGetLastError();
@@ -1152,10 +1129,6 @@ dc_status dc_create(const dc_config* cfg_in, const dc_mesh_desc* meshes, int32_t
         s.h_cnt = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * NCNT));
         s.h_flags = reinterpret_cast<int8_t*>(take((size_t)ne_max));
         s.h_out_cap = (size_t)ne_max;
-        if (serving(i)) {
-          s.h_faces = reinterpret_cast<double*>(take(sizeof(double) * stage));
-          s.h_faces_cap = stage;
-        }
       }
     }
   }

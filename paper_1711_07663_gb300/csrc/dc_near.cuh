@@ -8,7 +8,8 @@
 // so no branch and bound is needed:
 //   k_near_main    warp per candidate: node labels (nodes with both labels:
 //                  fringe); the faces whose boxes come within tol of the
-//                  element box, each converted once into the element frame;
+//                  element box, gathered into a list first and then taken 8
+//                  at a time, each converted once into the element frame;
 //                  the triangle pairs whose boxes come within tol (less the
 //                  rounding bound), 32 at a time: plane separation settles most,
 //                  a certified FP32 crossing makes the element fringe and ends

@@ -100,8 +100,8 @@ __device__ void surface_tile(Inst& in, long long f0, bool derive_grid) {
   if (threadIdx.x < 3) s_ext[threadIdx.x] = 0u;
   const double* src = in.faces_in + f0 * npf * 3;
   double* dst = in.surf + f0 * npf * 3;
-  // |v| >= 1e300 or not finite, tested on the bit pattern (32-bit words: the
-  // FP64 pipe of this GPU is slow)
+  // |v| >= 1e300 or not finite, tested on the bit pattern (integer words, no
+  // FP64 arithmetic: the FP64 pipe of this GPU is slow)
   const int bigh = (int)(__double_as_longlong(1e300) >> 32);
   const unsigned bigl = (unsigned)__double_as_longlong(1e300);
   auto huge = [&](double v) {

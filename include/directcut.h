@@ -157,7 +157,8 @@ typedef struct {
     float ms_holemap;         /* 0: part of ms_surface (kept for the layout) */
     float ms_classify;        /* 0: part of ms_surface (kept for the layout) */
     float ms_exact;           /* exact element-face tests + sign (main pass) */
-    float ms_redo;            /* FP64 pass over elements whose FP32 re-solve list overflowed */
+    float ms_redo;            /* FP64 pass over elements whose FP32 re-solve list overflowed
+                                 (flags-only form: over its full-search list) */
     float ms_total;
     int64_t near_tasks;       /* flags-only requests: (element, face) pairs of boxes within
                                  tol listed for the flat exact test */

@@ -612,12 +612,12 @@ dc_status launch_cut(dc_ctx* c, Slot& s, const LaunchParams& P, cudaStream_t st,
     CandList fl{P.full, (unsigned long long)ne_total, d_cnt + 20};
     CK(launch_k(true, kn, dim3(c->n_sm * occn), dim3(32 * wpc), sm, st, d_inst, cl, fl, nb, pmax, qmax, P.cpw,
                 d_cnt + 4));
+    if (prof) CK(record(s.ev[5], st, capturing));  // (the FP64 pass below is the "redo" phase)
     // the candidates it listed for the full per-element search -- only
     // elements with no labelled node that are not fringe (distances are never
     // asked for in this form), almost always none: a small FP64 pass
     CK(launch_k(true, k_exact<double>, dim3(std::min(c->n_sm, 16)), dim3(TB), (size_t)Ld.total * WPB, st, d_inst, fl,
                 none, pmax, qmax, d_cnt + 4));
-    if (prof) CK(record(s.ev[5], st, capturing));
   } else if (P.precision == DC_FP32_RECHECK) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_exact<float>, TB, (size_t)Lf.total * WPB);

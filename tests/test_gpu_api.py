@@ -107,6 +107,33 @@ def test_invalid_arguments_are_status_codes():
     assert ei.value.status == dc.DC_EINVAL
 
 
+@pytest.mark.parametrize("value", [np.nan, -np.nan, np.inf, -np.inf, 1e301, -1e301, 1e300])
+def test_huge_or_non_finite_coordinates_are_rejected(value):
+    # the grid's node boxes and the surface's face boxes are reduced on
+    # integer keys of the bit patterns; a coordinate of magnitude 1e300 or
+    # more, or not finite, anywhere in an element or a face, is an error
+    c = W.sphere_in_box(n=5, p=2, m=2, q=2, seed=4)
+    npe = c.nodes.shape[1]
+    for e, nd, a in ((0, 0, 0), (c.n_elem - 1, npe - 1, 2), (57, 13, 1)):
+        nodes = c.nodes.copy()
+        nodes[e, nd, a] = value
+        with pytest.raises(dc.DirectCutError) as ei:
+            dc.Context([(c.p, nodes)])
+        assert ei.value.status == dc.DC_EINVAL, (e, nd, a)
+    with dc.Context([(c.p, c.nodes)]) as ctx:
+        npf = c.faces.shape[1]
+        for f, nd, a in ((0, 0, 0), (c.n_faces - 1, npf - 1, 2), (5, 4, 1)):
+            faces = c.faces.copy()
+            faces[f, nd, a] = value
+            with pytest.raises(dc.DirectCutError) as ei:
+                ctx.cut(0, c.q, faces)
+            assert ei.value.status == dc.DC_EINVAL, (f, nd, a)
+        # and the context still cuts
+        f = ctx.cut(0, c.q, c.faces)
+        rf, _, _, _ = O.cut(c.p, c.nodes, c.q, c.faces)
+        assert np.array_equal(f, rf)
+
+
 def test_memory_budget_admission():
     c = W.sphere_in_box(n=8, p=2, m=4, q=2, seed=3)
     # nodes, float boxes, float element-frame nodes, frame origins
